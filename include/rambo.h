@@ -1,0 +1,192 @@
+/*
+ * rambo.h -- C ABI of the GB300 RAMBO library (librambo_gpu.so).
+ *
+ * RAMBO (Repeated And Merged BloOm filter; Gupta et al., SIGMOD'21) answers
+ * "which of K documents contain every k-mer of this sequence?".  It keeps an
+ * R x B table of Bloom filters ("BFUs", Section 2.1): in repetition r the K
+ * documents are partitioned into B buckets by a hash phi_r of the document id,
+ * and each bucket's documents are merged into one BFU of m bits probed by eta
+ * hash functions (Section 3, Algorithm 1).  A query ANDs, per BFU, the
+ * membership of all its k-mers, takes per repetition the union of the
+ * documents of the passing BFUs, and intersects the R unions (Algorithm 2,
+ * Section 3.3, Section 3.3.1).
+ *
+ * The library owns the index in GPU memory (HBM).  Every step of insertion
+ * and query runs in the library's CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Sequences   2-bit packed: base t of a buffer is in byte t>>2 at bits
+ *              2*(t&3)..2*(t&3)+1; A=0, C=1, G=2, T=3.  A batch is one packed
+ *              buffer plus CSR base offsets (n+1 uint64): item i is bases
+ *              [offsets[i], offsets[i+1]).  Offsets may start anywhere and
+ *              items may overlap.
+ *  Terms       canonical k-mers: min(forward code, reverse-complement code),
+ *              forward code = first base most significant (Section 3.3.1,
+ *              Section 5.1 "2-bit encoding"; canonical form is this library's
+ *              strand-independent reading).
+ *  Hashes      MurmurHash3_x64_128 over the 8-byte little-endian key, first
+ *              64-bit output word.  Probe j uses seed (uint32)(seed + j) and
+ *              is reduced mod m; document d goes to bucket
+ *              hash(d, (uint32)(seed + 1000 + r)) mod B.  All BFUs share the
+ *              probe positions (Section 5.3: every node uses the same h).
+ *  Masks       a query answer is a K-bit document mask of W = ceil(K/32)
+ *              uint32 words: document d is word d>>5, bit d&31; bits >= K are
+ *              zero.  Only inserted documents can appear.  A query with no
+ *              k-mer (length < k) returns every inserted document (Algorithm
+ *              2's "for all x in Q" holds vacuously).
+ *  Ownership   the caller owns every buffer it passes; the library keeps no
+ *              pointer after a call returns (device calls: after the work
+ *              enqueued on `stream` completes).  The library owns the index.
+ *  Errors      every int-returning call returns RAMBO_OK (0) or a negative
+ *              RAMBO_E* code; no exception crosses the ABI.  On error the
+ *              outputs are unspecified.  Argument errors are detected before
+ *              anything is enqueued, so the index is unchanged.  Device-side
+ *              checks of device-resident data (doc id >= K, bad k-mer code,
+ *              decreasing offsets) skip the offending item and latch an error
+ *              that rambo_sync() reports.
+ *  Threads     a handle is not thread-safe; serialise calls on one handle.
+ *              Inserts and queries are ordered by the stream they are enqueued
+ *              on (an insert is visible to every later query on that stream).
+ */
+#ifndef RAMBO_H
+#define RAMBO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RAMBO_OK 0
+#define RAMBO_EINVAL (-1)   /* bad argument (size, pointer, parameter, k-mer code) */
+#define RAMBO_ENOMEM (-2)   /* device or host allocation failed                  */
+#define RAMBO_ECUDA (-3)    /* a CUDA runtime call failed                        */
+#define RAMBO_ERANGE (-4)   /* document id >= K                                  */
+#define RAMBO_ETIMEOUT (-5) /* a bounded device wait gave up                     */
+#define RAMBO_ESTATE (-6)   /* call not valid in the handle's current state      */
+
+typedef struct rambo rambo_t;
+
+/* Layout facts of a handle (all sizes in bytes unless noted). */
+typedef struct {
+    uint32_t K, B, R, eta, k;
+    uint64_t m, seed;
+    uint32_t mask_words;     /* W = ceil(K/32)                                    */
+    uint32_t group_bytes;    /* bytes of one position group (all R*B bits of one */
+                             /* probe position; power of two up to 512, then     */
+                             /* multiples of 512)                                 */
+    uint64_t index_bytes;    /* m * group_bytes                                    */
+    uint64_t docbits_bytes;  /* R * B * W * 4: bucket -> document bitmaps         */
+    int device;              /* CUDA device ordinal the index lives on            */
+} rambo_info_t;
+
+/* Creates an empty index (Section 3.2, "RAMBO <- B x R array of Bloom
+ * Filters"; partition functions phi_r generated from `seed`).
+ *   K   number of documents (ids 0..K-1), >= 1
+ *   B   buckets (BFUs) per repetition, >= 1
+ *   R   repetitions, >= 1
+ *   m   bits per BFU, 1 <= m <= 2^32
+ *   eta Bloom hash functions, 1..64
+ *   k   k-mer length, 1..32
+ *   seed base seed of the hash functions
+ *   device CUDA device ordinal (-1 = the current device)
+ * Allocates m*group_bytes of index plus R*B*W*4 of bitmaps on the device and
+ * zeroes them.  Returns RAMBO_EINVAL on bad parameters, RAMBO_ENOMEM if the
+ * index does not fit.  *out is set only on success. */
+int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint32_t k,
+                 uint64_t seed, int device, rambo_t **out);
+
+/* Frees the index and every buffer the handle owns (waits for its work). */
+int rambo_destroy(rambo_t *h);
+
+/* W = ceil(K/32), the uint32 words of one answer mask (0 if h is NULL). */
+uint32_t rambo_mask_words(const rambo_t *h);
+
+int rambo_get_info(const rambo_t *h, rambo_info_t *info);
+
+/* Human-readable name of an error code (static string). */
+const char *rambo_strerror(int code);
+
+/* ---------------------------------------------------------------------- */
+/* Host-buffer calls: synchronous; inputs and outputs are host memory.     */
+/* The library stages the data through its own device workspace.          */
+
+/* Algorithm 1 for one document: every canonical k-mer of the n_bases bases
+ * starting at base 0 of `packed` is inserted into BFU (phi_r(doc_id), r) for
+ * every r.  Re-inserting a document or a k-mer is idempotent.  A document
+ * shorter than k is still registered (it has no terms).
+ * RAMBO_ERANGE if doc_id >= K. */
+int rambo_insert(rambo_t *h, uint32_t doc_id, const uint8_t *packed, uint64_t n_bases);
+
+/* Algorithm 1 for n_docs documents: document i has id doc_ids[i] and bases
+ * [base_offsets[i], base_offsets[i+1]) of `packed`.  base_offsets has
+ * n_docs+1 non-decreasing entries.  RAMBO_ERANGE if any id >= K (nothing is
+ * inserted then). */
+int rambo_insert_batch(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                       const uint8_t *packed, const uint64_t *base_offsets);
+
+/* Algorithm 2 for n single k-mers.  kmers[i] is a forward code (first base
+ * most significant, 2 bits per base); it is canonicalised inside.  A code
+ * with a bit set at or above 2k is RAMBO_EINVAL.  out receives n*W words
+ * (query i at out + i*W). */
+int rambo_query_kmers(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out);
+
+/* Section 3.3.1 sequence queries: the answer for sequence i (bases
+ * [base_offsets[i], base_offsets[i+1]) of `packed`) is the set of documents
+ * whose BFUs pass every k-mer of the sequence in every repetition.  out
+ * receives n*W words. */
+int rambo_query_seqs(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64_t *base_offsets,
+                     uint32_t *out);
+
+/* ---------------------------------------------------------------------- */
+/* Device-buffer calls: asynchronous on `stream` (a cudaStream_t, NULL =    */
+/* the legacy default stream).  Pointers are device memory.  Each call     */
+/* needs a caller-provided device workspace of at least the size returned  */
+/* by the matching *_workspace() call, 256-byte aligned; a workspace must   */
+/* not be shared by calls that may run at the same time.  `packed_bytes`   */
+/* bounds every read of `packed` (any alignment is accepted).  Errors       */
+/* found on the device are latched and reported by rambo_sync().            */
+
+size_t rambo_insert_workspace(const rambo_t *h, uint64_t n_docs);
+size_t rambo_query_kmers_workspace(const rambo_t *h, uint64_t n);
+size_t rambo_query_seqs_workspace(const rambo_t *h, uint64_t n);
+
+int rambo_insert_batch_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                           const uint8_t *packed, uint64_t packed_bytes,
+                           const uint64_t *base_offsets, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
+int rambo_query_kmers_dev(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
+                         const uint64_t *base_offsets, uint32_t *out, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* Waits for `stream` and returns the first device-side error latched since
+ * the last rambo_sync (then clears it), or RAMBO_OK. */
+int rambo_sync(rambo_t *h, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Introspection (host copies; synchronous).                               */
+
+/* Copies `nbytes` of the index starting at byte `offset` to host `dst`.
+ * The index is m position groups of group_bytes; in group p, bit r*B+b (word
+ * (r*B+b)>>5, bit (r*B+b)&31) is bit p of BFU (b, r). */
+int rambo_copy_index(const rambo_t *h, uint64_t offset, uint64_t nbytes, void *dst);
+
+/* Copies the R*B*W-word bucket->document bitmaps: bucket b of repetition r
+ * at words (r*B+b)*W .. +W; bit d set iff document d was inserted and
+ * phi_r(d) = b (DocIDs(M[b,r]) of Algorithm 2). */
+int rambo_copy_docbits(const rambo_t *h, uint32_t *dst);
+
+/* Copies phi: dst[d*R + r] = bucket of document d in repetition r. */
+int rambo_copy_partition(const rambo_t *h, uint32_t *dst);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAMBO_H */

@@ -1,0 +1,533 @@
+// rambo_api.cu -- the C ABI declared in include/rambo.h: handle lifetime,
+// argument checks, workspace layout, host staging and kernel sequencing.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "rambo.h"
+#include "rambo_internal.cuh"
+
+using namespace rgpu;
+
+struct rambo {
+    Geometry g;
+    int device;
+    int sm_count;
+    cudaStream_t stream;     // used by the host-buffer calls
+    uint32_t *d_index;       // m * Gw words
+    uint32_t *d_docbits;     // R * B * W words
+    uint32_t *d_phi;         // K * R
+    uint32_t *d_err;         // latched device error bits
+    void *d_stage;           // host-call staging + workspace
+    size_t stage_bytes;
+};
+
+namespace rgpu {
+
+Geometry make_geometry(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint32_t k,
+                       uint64_t seed) {
+    Geometry g{};
+    g.K = K; g.B = B; g.R = R; g.m = m; g.eta = eta; g.k = k; g.seed = seed;
+    g.W = (K + 31) / 32;
+    g.gbits = R * B;
+    const uint64_t raw = ((uint64_t)g.gbits + 31) / 32 * 4;  // bytes
+    uint64_t G;
+    if (raw <= 512) {
+        G = 4;
+        while (G < raw) G <<= 1;
+    } else {
+        G = (raw + 511) / 512 * 512;
+    }
+    g.Gw = (uint32_t)(G / 4);
+    if (G <= 16) {
+        g.SW = (uint32_t)(G / 4);
+        g.LPG = 1;
+        g.chunks = 1;
+    } else {
+        g.SW = 4;
+        g.LPG = (uint32_t)(G >= 512 ? 32 : G / 16);
+        g.chunks = (uint32_t)(G >= 512 ? G / 512 : 1);
+    }
+    return g;
+}
+
+}  // namespace rgpu
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return RAMBO_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RAMBO_ENOMEM;
+    }
+    return RAMBO_ECUDA;
+}
+
+#define RAMBO_TRY(expr)                         \
+    do {                                        \
+        const int rc_ = cuda_rc(expr);          \
+        if (rc_ != RAMBO_OK) return rc_;        \
+    } while (0)
+
+// Workspace layouts (offsets are 256-byte aligned).
+struct SeqWs {
+    size_t kcum, bsum, acc, total;
+};
+SeqWs seq_ws(const Geometry &g, uint64_t n) {
+    SeqWs w;
+    w.kcum = 0;
+    w.bsum = align_up((n + 1) * 8);
+    w.acc = w.bsum + align_up((kmer_prefix_block_sums(n) + 1) * 8);
+    w.total = w.acc + align_up(n * (uint64_t)g.Gw * 4);
+    return w;
+}
+
+size_t kmers_ws(const Geometry &g, uint64_t n) { return align_up(n * (uint64_t)g.Gw * 4); }
+
+struct InsWs {
+    size_t kcum, bsum, total;
+};
+InsWs ins_ws(uint64_t n) {
+    InsWs w;
+    w.kcum = 0;
+    w.bsum = align_up((n + 1) * 8);
+    w.total = w.bsum + align_up((kmer_prefix_block_sums(n) + 1) * 8);
+    return w;
+}
+
+int reserve_stage(rambo_t *h, size_t bytes) {
+    if (bytes <= h->stage_bytes) return RAMBO_OK;
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    if (h->d_stage) cudaFree(h->d_stage);
+    h->d_stage = nullptr;
+    h->stage_bytes = 0;
+    size_t want = bytes + bytes / 4;
+    RAMBO_TRY(cudaMalloc(&h->d_stage, want));
+    h->stage_bytes = want;
+    return RAMBO_OK;
+}
+
+// Packed pointers of any alignment: read from the 8-byte aligned address
+// below and shift every base offset by the bytes in between.
+struct Aligned {
+    const uint8_t *p;
+    uint64_t bytes;
+    uint64_t base_shift;
+};
+Aligned align_packed(const uint8_t *packed, uint64_t packed_bytes) {
+    const uintptr_t mis = reinterpret_cast<uintptr_t>(packed) & 7;
+    return Aligned{packed - mis, packed_bytes + mis, (uint64_t)mis * 4};
+}
+
+int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
+                       const uint64_t *offsets, uint32_t *out, void *ws, cudaStream_t s) {
+    const Geometry &g = h->g;
+    const SeqWs L = seq_ws(g, n);
+    char *w = static_cast<char *>(ws);
+    uint64_t *kcum = reinterpret_cast<uint64_t *>(w + L.kcum);
+    uint64_t *bsum = reinterpret_cast<uint64_t *>(w + L.bsum);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(w + L.acc);
+    const Aligned al = align_packed(packed, packed_bytes);
+    RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+    RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
+    ProbeArgs a{};
+    a.index = h->d_index;
+    a.m = g.m;
+    a.m_pow2 = (g.m & (g.m - 1)) == 0;
+    a.Gw = g.Gw;
+    a.eta = g.eta;
+    a.k = g.k;
+    a.seed32 = (uint32_t)g.seed;
+    a.packed = al.p;
+    a.packed_bytes = al.bytes;
+    a.base_shift = al.base_shift;
+    a.offsets = offsets;
+    a.kcum = kcum;
+    a.n = n;
+    a.acc = acc;
+    a.err = h->d_err;
+    RAMBO_TRY(launch_probe_seqs(a, g, h->sm_count, s));
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out};
+    RAMBO_TRY(launch_expand(e, h->sm_count, s));
+    return RAMBO_OK;
+}
+
+int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out, void *ws,
+                        cudaStream_t s) {
+    const Geometry &g = h->g;
+    uint32_t *acc = static_cast<uint32_t *>(ws);
+    if (g.eta > 4) RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
+    ProbeArgs a{};
+    a.index = h->d_index;
+    a.m = g.m;
+    a.m_pow2 = (g.m & (g.m - 1)) == 0;
+    a.Gw = g.Gw;
+    a.eta = g.eta;
+    a.k = g.k;
+    a.seed32 = (uint32_t)g.seed;
+    a.kmers = kmers;
+    a.n = n;
+    a.acc = acc;
+    a.err = h->d_err;
+    RAMBO_TRY(launch_probe_kmers(a, g, h->sm_count, s));
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out};
+    RAMBO_TRY(launch_expand(e, h->sm_count, s));
+    return RAMBO_OK;
+}
+
+int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_t *packed,
+                   uint64_t packed_bytes, const uint64_t *offsets, void *ws, cudaStream_t s) {
+    const Geometry &g = h->g;
+    const InsWs L = ins_ws(n);
+    char *w = static_cast<char *>(ws);
+    uint64_t *kcum = reinterpret_cast<uint64_t *>(w + L.kcum);
+    uint64_t *bsum = reinterpret_cast<uint64_t *>(w + L.bsum);
+    const Aligned al = align_packed(packed, packed_bytes);
+    RAMBO_TRY(launch_register_docs(doc_ids, n, h->d_phi, g.K, g.R, g.B, g.W, h->d_docbits, h->d_err, s));
+    RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+    InsertArgs a{};
+    a.index = h->d_index;
+    a.m = g.m;
+    a.m_pow2 = (g.m & (g.m - 1)) == 0;
+    a.Gw = g.Gw;
+    a.B = g.B;
+    a.R = g.R;
+    a.K = g.K;
+    a.eta = g.eta;
+    a.k = g.k;
+    a.seed32 = (uint32_t)g.seed;
+    a.phi = h->d_phi;
+    a.doc_ids = doc_ids;
+    a.packed = al.p;
+    a.packed_bytes = al.bytes;
+    a.base_shift = al.base_shift;
+    a.offsets = offsets;
+    a.kcum = kcum;
+    a.n = n;
+    a.err = h->d_err;
+    RAMBO_TRY(launch_insert(a, h->sm_count, s));
+    return RAMBO_OK;
+}
+
+// Reads and clears the latched error word on the handle's own stream (the
+// caller has already waited for the stream the kernels ran on).
+int read_and_clear_err(rambo_t *h) {
+    uint32_t e = 0;
+    RAMBO_TRY(cudaMemcpyAsync(&e, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream));
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    if (e) {
+        RAMBO_TRY(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+        RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    }
+    if (e & ERR_DOC_RANGE) return RAMBO_ERANGE;
+    if (e & (ERR_KMER_CODE | ERR_OFFSETS)) return RAMBO_EINVAL;
+    return RAMBO_OK;
+}
+
+bool offsets_ok(uint64_t n, const uint64_t *offs) {
+    for (uint64_t i = 0; i < n; ++i)
+        if (offs[i + 1] < offs[i]) return false;
+    return true;
+}
+
+// Copies the bytes holding bases [offs[0], offs[n]) of a host batch into the
+// staging buffer (plus 16 zero bytes) and rebased offsets after it.
+struct Staged {
+    uint8_t *packed;
+    uint64_t packed_bytes;
+    uint64_t *offsets;
+    char *rest;
+};
+int stage_batch(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64_t *offs, size_t extra,
+                Staged *st) {
+    const uint64_t b_lo = offs[0] >> 2;
+    const uint64_t b_hi = (offs[n] + 3) >> 2;
+    const uint64_t nbytes = b_hi - b_lo;
+    const size_t p_sz = align_up(nbytes + 16);
+    const size_t o_sz = align_up((n + 1) * 8);
+    int rc = reserve_stage(h, p_sz + o_sz + extra);
+    if (rc) return rc;
+    char *base = static_cast<char *>(h->d_stage);
+    st->packed = reinterpret_cast<uint8_t *>(base);
+    st->packed_bytes = nbytes;
+    st->offsets = reinterpret_cast<uint64_t *>(base + p_sz);
+    st->rest = base + p_sz + o_sz;
+    uint64_t *reb = static_cast<uint64_t *>(std::malloc((n + 1) * 8));
+    if (!reb) return RAMBO_ENOMEM;
+    for (uint64_t i = 0; i <= n; ++i) reb[i] = offs[i] - 4 * b_lo;
+    cudaError_t e = cudaMemcpyAsync(st->packed, packed + b_lo, nbytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st->packed + nbytes, 0, 16, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st->offsets, reb, (n + 1) * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // reb is freed next
+    std::free(reb);
+    return cuda_rc(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rambo_strerror(int code) {
+    switch (code) {
+        case RAMBO_OK: return "ok";
+        case RAMBO_EINVAL: return "invalid argument";
+        case RAMBO_ENOMEM: return "out of memory";
+        case RAMBO_ECUDA: return "CUDA runtime error";
+        case RAMBO_ERANGE: return "document id out of range";
+        case RAMBO_ETIMEOUT: return "device wait timed out";
+        case RAMBO_ESTATE: return "invalid state";
+        default: return "unknown error";
+    }
+}
+
+int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint32_t k,
+                 uint64_t seed, int device, rambo_t **out) {
+    if (!out || K == 0 || B == 0 || R == 0 || m == 0 || m > (1ULL << 32) || eta == 0 || eta > 64 ||
+        k == 0 || k > 32)
+        return RAMBO_EINVAL;
+    if ((uint64_t)R * B > (1ULL << 24)) return RAMBO_EINVAL;
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) return RAMBO_ECUDA;
+    DeviceGuard guard(device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    rambo_t *h = new (std::nothrow) rambo();
+    if (!h) return RAMBO_ENOMEM;
+    h->g = make_geometry(K, B, R, m, eta, k, seed);
+    h->device = device;
+    int rc = RAMBO_OK;
+    auto fail = [&](int code) {
+        rambo_destroy(h);
+        return code;
+    };
+    if ((rc = cuda_rc(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device))))
+        return fail(rc);
+    if ((rc = cuda_rc(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)))) return fail(rc);
+    const uint64_t index_bytes = m * (uint64_t)h->g.Gw * 4;
+    const uint64_t docbits_bytes = (uint64_t)R * B * h->g.W * 4;
+    if ((rc = cuda_rc(cudaMalloc(&h->d_index, index_bytes)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&h->d_docbits, docbits_bytes)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&h->d_phi, (uint64_t)K * R * 4)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&h->d_err, 4)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemsetAsync(h->d_index, 0, index_bytes, h->stream)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemsetAsync(h->d_docbits, 0, docbits_bytes, h->stream)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemsetAsync(h->d_err, 0, 4, h->stream)))) return fail(rc);
+    if ((rc = cuda_rc(launch_partition(h->d_phi, K, R, B, seed, h->stream)))) return fail(rc);
+    if ((rc = cuda_rc(cudaStreamSynchronize(h->stream)))) return fail(rc);
+    *out = h;
+    return RAMBO_OK;
+}
+
+int rambo_destroy(rambo_t *h) {
+    if (!h) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_index);
+    cudaFree(h->d_docbits);
+    cudaFree(h->d_phi);
+    cudaFree(h->d_err);
+    cudaFree(h->d_stage);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return RAMBO_OK;
+}
+
+uint32_t rambo_mask_words(const rambo_t *h) { return h ? h->g.W : 0; }
+
+int rambo_get_info(const rambo_t *h, rambo_info_t *info) {
+    if (!h || !info) return RAMBO_EINVAL;
+    const Geometry &g = h->g;
+    info->K = g.K; info->B = g.B; info->R = g.R; info->eta = g.eta; info->k = g.k;
+    info->m = g.m; info->seed = g.seed;
+    info->mask_words = g.W;
+    info->group_bytes = g.Gw * 4;
+    info->index_bytes = g.m * (uint64_t)g.Gw * 4;
+    info->docbits_bytes = (uint64_t)g.R * g.B * g.W * 4;
+    info->device = h->device;
+    return RAMBO_OK;
+}
+
+size_t rambo_insert_workspace(const rambo_t *h, uint64_t n_docs) {
+    return h ? ins_ws(n_docs).total : 0;
+}
+size_t rambo_query_kmers_workspace(const rambo_t *h, uint64_t n) {
+    return h ? kmers_ws(h->g, n) : 0;
+}
+size_t rambo_query_seqs_workspace(const rambo_t *h, uint64_t n) {
+    return h ? seq_ws(h->g, n).total : 0;
+}
+
+// ----------------------------------------------------------------- device
+
+int rambo_insert_batch_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                           const uint8_t *packed, uint64_t packed_bytes,
+                           const uint64_t *base_offsets, void *workspace, size_t workspace_bytes,
+                           void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n_docs == 0) return RAMBO_OK;
+    if (!doc_ids || !base_offsets || !workspace || (!packed && packed_bytes) ||
+        workspace_bytes < ins_ws(n_docs).total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    return insert_enqueue(h, n_docs, doc_ids, packed, packed_bytes, base_offsets, workspace,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int rambo_query_kmers_dev(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n == 0) return RAMBO_OK;
+    if (!kmers || !out || !workspace || workspace_bytes < kmers_ws(h->g, n) ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    return query_kmers_enqueue(h, n, kmers, out, workspace, static_cast<cudaStream_t>(stream));
+}
+
+int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
+                         const uint64_t *base_offsets, uint32_t *out, void *workspace,
+                         size_t workspace_bytes, void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n == 0) return RAMBO_OK;
+    if (n >= 0xffffffffULL || !base_offsets || !out || !workspace || (!packed && packed_bytes) ||
+        workspace_bytes < seq_ws(h->g, n).total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    return query_seqs_enqueue(h, n, packed, packed_bytes, base_offsets, out, workspace,
+                              static_cast<cudaStream_t>(stream));
+}
+
+int rambo_sync(rambo_t *h, void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    RAMBO_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return read_and_clear_err(h);
+}
+
+// ------------------------------------------------------------------- host
+
+int rambo_insert_batch(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                       const uint8_t *packed, const uint64_t *base_offsets) {
+    if (!h) return RAMBO_EINVAL;
+    if (n_docs == 0) return RAMBO_OK;
+    if (!doc_ids || !base_offsets || !offsets_ok(n_docs, base_offsets)) return RAMBO_EINVAL;
+    if (!packed && base_offsets[n_docs] > base_offsets[0]) return RAMBO_EINVAL;
+    for (uint32_t i = 0; i < n_docs; ++i)
+        if (doc_ids[i] >= h->g.K) return RAMBO_ERANGE;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    const size_t ids_sz = align_up((size_t)n_docs * 4);
+    Staged st;
+    int rc = stage_batch(h, n_docs, packed, base_offsets, ids_sz + ins_ws(n_docs).total, &st);
+    if (rc) return rc;
+    uint32_t *d_ids = reinterpret_cast<uint32_t *>(st.rest);
+    RAMBO_TRY(cudaMemcpyAsync(d_ids, doc_ids, (size_t)n_docs * 4, cudaMemcpyHostToDevice, h->stream));
+    rc = insert_enqueue(h, n_docs, d_ids, st.packed, st.packed_bytes + 16, st.offsets,
+                        st.rest + ids_sz, h->stream);
+    if (rc) return rc;
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    return read_and_clear_err(h);
+}
+
+int rambo_insert(rambo_t *h, uint32_t doc_id, const uint8_t *packed, uint64_t n_bases) {
+    const uint64_t offs[2] = {0, n_bases};
+    return rambo_insert_batch(h, 1, &doc_id, packed, offs);
+}
+
+int rambo_query_kmers(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out) {
+    if (!h) return RAMBO_EINVAL;
+    if (n == 0) return RAMBO_OK;
+    if (!kmers || !out) return RAMBO_EINVAL;
+    const uint64_t bad = h->g.k >= 32 ? 0 : ~((1ULL << (2 * h->g.k)) - 1);
+    for (uint64_t i = 0; i < n; ++i)
+        if (kmers[i] & bad) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    const size_t in_sz = align_up(n * 8), out_sz = align_up(n * (uint64_t)h->g.W * 4);
+    int rc = reserve_stage(h, in_sz + out_sz + kmers_ws(h->g, n));
+    if (rc) return rc;
+    char *base = static_cast<char *>(h->d_stage);
+    uint64_t *d_k = reinterpret_cast<uint64_t *>(base);
+    uint32_t *d_out = reinterpret_cast<uint32_t *>(base + in_sz);
+    RAMBO_TRY(cudaMemcpyAsync(d_k, kmers, n * 8, cudaMemcpyHostToDevice, h->stream));
+    rc = query_kmers_enqueue(h, n, d_k, d_out, base + in_sz + out_sz, h->stream);
+    if (rc) return rc;
+    RAMBO_TRY(cudaMemcpyAsync(out, d_out, n * (uint64_t)h->g.W * 4, cudaMemcpyDeviceToHost, h->stream));
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    return read_and_clear_err(h);
+}
+
+int rambo_query_seqs(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64_t *base_offsets,
+                     uint32_t *out) {
+    if (!h) return RAMBO_EINVAL;
+    if (n == 0) return RAMBO_OK;
+    if (n >= 0xffffffffULL || !base_offsets || !out || !offsets_ok(n, base_offsets)) return RAMBO_EINVAL;
+    if (!packed && base_offsets[n] > base_offsets[0]) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    const size_t out_sz = align_up(n * (uint64_t)h->g.W * 4);
+    Staged st;
+    int rc = stage_batch(h, n, packed, base_offsets, out_sz + seq_ws(h->g, n).total, &st);
+    if (rc) return rc;
+    uint32_t *d_out = reinterpret_cast<uint32_t *>(st.rest);
+    rc = query_seqs_enqueue(h, n, st.packed, st.packed_bytes + 16, st.offsets, d_out,
+                            st.rest + out_sz, h->stream);
+    if (rc) return rc;
+    RAMBO_TRY(cudaMemcpyAsync(out, d_out, n * (uint64_t)h->g.W * 4, cudaMemcpyDeviceToHost, h->stream));
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    return read_and_clear_err(h);
+}
+
+// --------------------------------------------------------- introspection
+
+int rambo_copy_index(const rambo_t *h, uint64_t offset, uint64_t nbytes, void *dst) {
+    if (!h || (!dst && nbytes)) return RAMBO_EINVAL;
+    const uint64_t total = h->g.m * (uint64_t)h->g.Gw * 4;
+    if (offset > total || nbytes > total - offset) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    RAMBO_TRY(cudaMemcpy(dst, reinterpret_cast<const char *>(h->d_index) + offset, nbytes,
+                         cudaMemcpyDeviceToHost));
+    return RAMBO_OK;
+}
+
+int rambo_copy_docbits(const rambo_t *h, uint32_t *dst) {
+    if (!h || !dst) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    RAMBO_TRY(cudaMemcpy(dst, h->d_docbits, (uint64_t)h->g.R * h->g.B * h->g.W * 4,
+                         cudaMemcpyDeviceToHost));
+    return RAMBO_OK;
+}
+
+int rambo_copy_partition(const rambo_t *h, uint32_t *dst) {
+    if (!h || !dst) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    RAMBO_TRY(cudaMemcpy(dst, h->d_phi, (uint64_t)h->g.K * h->g.R * 4, cudaMemcpyDeviceToHost));
+    return RAMBO_OK;
+}
+
+}  // extern "C"

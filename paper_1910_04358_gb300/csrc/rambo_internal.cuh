@@ -1,0 +1,227 @@
+// rambo_internal.cuh -- device helpers and kernel launchers shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rgpu {
+
+// ---------------------------------------------------------------------------
+// Device error word bits (latched by kernels, read by rambo_sync).
+enum : uint32_t {
+    ERR_DOC_RANGE = 1u,     // document id >= K
+    ERR_KMER_CODE = 2u,     // k-mer code with a bit at or above 2k
+    ERR_OFFSETS = 4u,       // decreasing offsets or offsets past the buffer
+};
+
+// ---------------------------------------------------------------------------
+// MurmurHash3_x64_128 restricted to one 8-byte key (the only key length the
+// index hashes).  The key block is mixed once (independent of the seed);
+// each seed then costs the two finalisers.  First output word only.
+
+__device__ __forceinline__ uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return k;
+}
+
+// Mixed key block k1 of an 8-byte key (the key is the whole "tail").
+__device__ __forceinline__ uint64_t mh_mix_key(uint64_t key) {
+    uint64_t k1 = key * 0x87c37b91114253d5ULL;
+    k1 = rotl64(k1, 31);
+    return k1 * 0x4cf5ad432745937fULL;
+}
+
+// First output word for a mixed key and a 32-bit seed (length 8).
+__device__ __forceinline__ uint64_t mh_first_word(uint64_t k1mix, uint32_t seed) {
+    uint64_t h1 = (uint64_t)seed ^ k1mix ^ 8ULL;
+    uint64_t h2 = (uint64_t)seed ^ 8ULL;
+    h1 += h2;
+    h2 += h1;
+    return fmix64(h1) + fmix64(h2);
+}
+
+// ---------------------------------------------------------------------------
+// k-mers from the 2-bit packed stream.
+
+// 64-bit little-endian word wi of a byte buffer of nbytes bytes whose start
+// is 8-byte aligned; bytes at or past nbytes read as zero and are not touched.
+__device__ __forceinline__ uint64_t ld_stream_word(const uint8_t *p, uint64_t nbytes, uint64_t wi) {
+    uint64_t b = wi * 8;
+    if (b + 8 <= nbytes) return __ldg(reinterpret_cast<const unsigned long long *>(p) + wi);
+    uint64_t v = 0;
+    for (int i = 0; i < 8; ++i)
+        if (b + i < nbytes) v |= (uint64_t)__ldg(p + b + i) << (8 * i);
+    return v;
+}
+
+// The 32 bases starting at base t, base t+i in bits 2i..2i+1.
+__device__ __forceinline__ uint64_t base_window(const uint8_t *p, uint64_t nbytes, uint64_t t) {
+    uint64_t bit = t * 2;
+    uint64_t wi = bit >> 6;
+    int sh = (int)(bit & 63);
+    uint64_t lo = ld_stream_word(p, nbytes, wi);
+    if (sh == 0) return lo;
+    uint64_t hi = ld_stream_word(p, nbytes, wi + 1);
+    return (lo >> sh) | (hi << (64 - sh));
+}
+
+// Reverses the order of the 32 two-bit digits of a 64-bit word.
+__device__ __forceinline__ uint64_t reverse_digits(uint64_t x) {
+    uint64_t y = __brevll(x);
+    return ((y >> 1) & 0x5555555555555555ULL) | ((y & 0x5555555555555555ULL) << 1);
+}
+
+__device__ __forceinline__ uint64_t kmask(uint32_t k) {
+    return k >= 32 ? ~0ULL : ((1ULL << (2 * k)) - 1);
+}
+
+// Canonical code of the k-mer whose bases sit least-significant-first in x:
+// the reverse complement is the digit-wise complement of x read as is, the
+// forward code is x with its digits reversed.
+__device__ __forceinline__ uint64_t canonical_from_window(uint64_t x, uint32_t k) {
+    uint64_t mask = kmask(k);
+    uint64_t rc = ~x & mask;
+    uint64_t fwd = reverse_digits(x) >> (64 - 2 * k);
+    return fwd < rc ? fwd : rc;
+}
+
+// Canonical code of a forward code (first base most significant).
+__device__ __forceinline__ uint64_t canonical_from_forward(uint64_t fwd, uint32_t k) {
+    uint64_t x = reverse_digits(fwd) >> (64 - 2 * k);  // bases least significant first
+    uint64_t rc = ~x & kmask(k);
+    return fwd < rc ? fwd : rc;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming loads of index slices (read once: no L1 allocation).
+
+template <int SW>
+struct Slice;
+template <>
+struct Slice<1> {
+    uint32_t w[1];
+};
+template <>
+struct Slice<2> {
+    uint32_t w[2];
+};
+template <>
+struct Slice<4> {
+    uint32_t w[4];
+};
+
+template <int SW>
+__device__ __forceinline__ Slice<SW> ld_slice(const uint32_t *p);
+
+template <>
+__device__ __forceinline__ Slice<1> ld_slice<1>(const uint32_t *p) {
+    Slice<1> s;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(s.w[0]) : "l"(p));
+    return s;
+}
+template <>
+__device__ __forceinline__ Slice<2> ld_slice<2>(const uint32_t *p) {
+    Slice<2> s;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(s.w[0]), "=r"(s.w[1]) : "l"(p));
+    return s;
+}
+template <>
+__device__ __forceinline__ Slice<4> ld_slice<4>(const uint32_t *p) {
+    Slice<4> s;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(s.w[0]), "=r"(s.w[1]), "=r"(s.w[2]), "=r"(s.w[3])
+        : "l"(p));
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of the bit-sliced index: m position groups, group p holding bit p
+// of every BFU; BFU (b, r) is bit r*B+b of the group.
+
+struct Geometry {
+    uint32_t K, B, R, eta, k;
+    uint64_t m;
+    uint64_t seed;
+    uint32_t W;        // mask words
+    uint32_t gbits;    // R*B
+    uint32_t Gw;       // words per group
+    uint32_t SW;       // words per lane slice (1, 2 or 4)
+    uint32_t LPG;      // lanes per group chunk (1..32)
+    uint32_t chunks;   // group chunks of LPG*SW words (G > 512 bytes)
+};
+
+Geometry make_geometry(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint32_t k,
+                       uint64_t seed);
+
+// Arguments of the probe kernels.
+struct ProbeArgs {
+    const uint32_t *index;
+    uint64_t m;
+    uint32_t m_pow2;      // m is a power of two: reduce with a mask
+    uint32_t Gw;
+    uint32_t eta;
+    uint32_t k;
+    uint32_t seed32;      // (uint32) seed
+    // sequence batch
+    const uint8_t *packed;   // 8-byte aligned base of the packed stream
+    uint64_t packed_bytes;   // readable bytes from `packed`
+    uint64_t base_shift;     // bases to add to every offset (alignment fix-up)
+    const uint64_t *offsets; // n+1
+    const uint64_t *kcum;    // n+1 exclusive prefix of k-mer counts
+    uint64_t n;
+    // single k-mers
+    const uint64_t *kmers;
+    // output: per query Gw words (bucket-space AND over its k-mers)
+    uint32_t *acc;
+    uint32_t *err;
+};
+
+struct ExpandArgs {
+    const uint32_t *acc;     // n x Gw
+    uint64_t n;
+    uint32_t Gw, B, R, W;
+    const uint32_t *docbits; // R*B*W
+    uint32_t *out;           // n x W
+};
+
+struct InsertArgs {
+    uint32_t *index;
+    uint64_t m;
+    uint32_t m_pow2;
+    uint32_t Gw, B, R, K, eta, k, seed32;
+    const uint32_t *phi;       // K x R
+    const uint32_t *doc_ids;   // n
+    const uint8_t *packed;
+    uint64_t packed_bytes;
+    uint64_t base_shift;
+    const uint64_t *offsets;   // n+1
+    const uint64_t *kcum;      // n+1
+    uint64_t n;
+    uint32_t *err;
+};
+
+// Launchers (rambo_kernels_*.cu).  All enqueue on `s` and return the launch
+// status.
+cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, uint64_t seed,
+                             cudaStream_t s);
+cudaError_t launch_kmer_prefix(const uint64_t *offsets, uint64_t n, uint32_t k, uint64_t base_shift,
+                               uint64_t packed_bytes, uint64_t *kcum, uint64_t *block_sums,
+                               uint32_t *err, cudaStream_t s);
+size_t kmer_prefix_block_sums(uint64_t n);
+cudaError_t launch_register_docs(const uint32_t *doc_ids, uint64_t n, const uint32_t *phi,
+                                 uint32_t K, uint32_t R, uint32_t B, uint32_t W, uint32_t *docbits,
+                                 uint32_t *err, cudaStream_t s);
+cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s);
+cudaError_t launch_probe_seqs(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
+cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
+cudaError_t launch_expand(const ExpandArgs &a, int sm_count, cudaStream_t s);
+
+}  // namespace rgpu

@@ -1,0 +1,258 @@
+// rambo_kernels_build.cu -- index construction and batch bookkeeping.
+//
+//   partition  phi_r(d) for every document and repetition (Section 3.2).
+//   prefix     exclusive prefix of the k-mer counts of a batch, so that the
+//              k-mers of all items form one flat index space [0, T).
+//   register   DocIDs(M[phi_r(d), r]) += d, as bits of the bucket->document
+//              bitmaps (Algorithm 2's DocIDs, the "inverted index mapping B
+//              buckets to K documents" of Section 5.2).
+//   insert     Algorithm 1: every k-mer x of document d sets bits
+//              h_1(x)..h_eta(x) of BFU (phi_r(d), r) for every r.  In the
+//              bit-sliced layout that is bit r*B+phi_r(d) of position group
+//              h_j(x); lanes of a warp that hit the same word are combined
+//              (warp-aggregated atomicOr) before one atomic is issued.
+#include "rambo_internal.cuh"
+
+namespace rgpu {
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+__global__ void k_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, uint64_t seed) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (uint64_t)K * R) return;
+    const uint32_t d = (uint32_t)(i / R), r = (uint32_t)(i % R);
+    const uint64_t h = mh_first_word(mh_mix_key((uint64_t)d), (uint32_t)(seed + 1000 + r));
+    phi[i] = (uint32_t)(h % B);
+}
+
+// -------------------------------------------------------------- prefix scan
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr uint64_t SCAN_TILE = (uint64_t)SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint64_t kmer_count(const uint64_t *offs, uint64_t i, uint32_t k,
+                                               uint64_t limit, uint32_t *err) {
+    const uint64_t b0 = offs[i], b1 = offs[i + 1];
+    if (b1 < b0 || b1 > limit) {
+        if (err) atomicOr(err, ERR_OFFSETS);
+        return 0;
+    }
+    const uint64_t L = b1 - b0;
+    return L >= k ? L - k + 1 : 0;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the prefix and
+// writes the block total to *total.
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *total) {
+    __shared__ uint64_t warp_sums[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t s = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t y = __shfl_up_sync(FULL, s, off);
+            if (lane >= off) s += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = s;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const uint64_t before = wid ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[SCAN_THREADS / 32 - 1];
+    __syncthreads();
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_prefix_partial(const uint64_t *offs, uint64_t n, uint32_t k, uint64_t limit, uint64_t *bsum,
+                 uint32_t *err) {
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    uint64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * SCAN_THREADS + threadIdx.x;
+        if (i < n) s += kmer_count(offs, i, k, limit, err);
+    }
+    uint64_t total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the block sums in place; kcum[n] = grand total.
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_prefix_blocks(uint64_t *bsum, uint64_t nblk, uint64_t *kcum, uint64_t n) {
+    uint64_t carry = 0;
+    for (uint64_t b0 = 0; b0 < nblk; b0 += SCAN_THREADS) {
+        const uint64_t i = b0 + threadIdx.x;
+        const uint64_t v = i < nblk ? bsum[i] : 0;
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan(v, &total);
+        if (i < nblk) bsum[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) kcum[n] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_prefix_final(const uint64_t *offs, uint64_t n, uint32_t k, uint64_t limit, const uint64_t *bsum,
+               uint64_t *kcum) {
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    uint64_t carry = bsum[blockIdx.x];
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * SCAN_THREADS + threadIdx.x;
+        const uint64_t c = i < n ? kmer_count(offs, i, k, limit, nullptr) : 0;
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan(c, &total);
+        if (i < n) kcum[i] = carry + ex;
+        carry += total;
+    }
+}
+
+// ------------------------------------------------------------- registration
+__global__ void k_register(const uint32_t *doc_ids, uint64_t n, const uint32_t *phi, uint32_t K,
+                           uint32_t R, uint32_t B, uint32_t W, uint32_t *docbits, uint32_t *err) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * R) return;
+    const uint64_t item = i / R;
+    const uint32_t r = (uint32_t)(i % R);
+    const uint32_t d = doc_ids[item];
+    if (d >= K) {
+        if (r == 0) atomicOr(err, ERR_DOC_RANGE);
+        return;
+    }
+    const uint32_t b = phi[(uint64_t)d * R + r];
+    atomicOr(&docbits[((uint64_t)r * B + b) * W + (d >> 5)], 1u << (d & 31));
+}
+
+// ------------------------------------------------------------------- insert
+constexpr int INSERT_THREADS = 256;
+
+template <int ETA>
+__global__ void __launch_bounds__(INSERT_THREADS, 1) k_insert(InsertArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t T = a.kcum[a.n];
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    uint64_t per = (T + nwarps - 1) / nwarps;
+    per = (per + 31) / 32 * 32;
+    if (per < 64) per = 64;
+    const uint64_t c0 = warp * per;
+    if (c0 >= T) return;
+    const uint64_t c1 = c0 + per < T ? c0 + per : T;
+
+    // document of the warp's first k-mer (largest i with kcum[i] <= c0)
+    uint64_t lo = 0, hi = a.n;
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a.kcum[mid] <= c0) lo = mid;
+        else hi = mid;
+    }
+    const uint64_t i_first = lo;
+
+    for (uint32_t jb = 0; jb < a.eta; jb += ETA) {
+        uint64_t item = i_first;
+        for (uint64_t base = c0; base < c1; base += 32) {
+            const uint64_t g = base + lane;
+            bool val = g < c1;
+            uint32_t d = 0;
+            uint64_t c = 0;
+            if (val) {
+                while (a.kcum[item + 1] <= g) ++item;
+                d = a.doc_ids[item];
+                if (d >= a.K) {
+                    val = false;
+                } else {
+                    const uint64_t start = a.offsets[item] + a.base_shift + (g - a.kcum[item]);
+                    c = canonical_from_window(base_window(a.packed, a.packed_bytes, start), a.k);
+                }
+            }
+            const uint64_t km = mh_mix_key(c);
+#pragma unroll
+            for (int e = 0; e < ETA; ++e) {
+                if (jb + e >= a.eta) break;  // warp-uniform
+                const uint64_t h = mh_first_word(km, a.seed32 + jb + e);
+                const uint64_t p = a.m_pow2 ? (h & (a.m - 1)) : (h % a.m);
+                for (uint32_t r = 0; r < a.R; ++r) {
+                    uint64_t addr = ~0ULL;
+                    uint32_t bit = 0;
+                    if (val) {
+                        const uint32_t bb = r * a.B + a.phi[(uint64_t)d * a.R + r];
+                        addr = p * a.Gw + (bb >> 5);
+                        bit = 1u << (bb & 31);
+                    }
+                    const uint32_t peers = __match_any_sync(FULL, addr);
+                    const uint32_t v = __reduce_or_sync(peers, bit);
+                    if (val && lane == __ffs(peers) - 1) atomicOr(a.index + addr, v);
+                }
+            }
+        }
+    }
+}
+
+template <typename KernelT>
+int blocks_per_sm(KernelT kernel, int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
+}
+
+template <int ETA>
+cudaError_t launch_insert_t(const InsertArgs &a, int sm_count, cudaStream_t s) {
+    static int occ = blocks_per_sm(k_insert<ETA>, INSERT_THREADS);
+    k_insert<ETA><<<sm_count * occ, INSERT_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, uint64_t seed,
+                             cudaStream_t s) {
+    const uint64_t n = (uint64_t)K * R;
+    k_partition<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(phi, K, R, B, seed);
+    return cudaGetLastError();
+}
+
+size_t kmer_prefix_block_sums(uint64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE); }
+
+cudaError_t launch_kmer_prefix(const uint64_t *offsets, uint64_t n, uint32_t k, uint64_t base_shift,
+                               uint64_t packed_bytes, uint64_t *kcum, uint64_t *block_sums,
+                               uint32_t *err, cudaStream_t s) {
+    (void)base_shift;
+    const uint64_t limit = packed_bytes * 4;  // bases addressable from the caller's pointer
+    const uint64_t nblk = kmer_prefix_block_sums(n);
+    if (nblk == 0) return cudaSuccess;
+    k_prefix_partial<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(offsets, n, k, limit, block_sums, err);
+    k_prefix_blocks<<<1, SCAN_THREADS, 0, s>>>(block_sums, nblk, kcum, n);
+    k_prefix_final<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(offsets, n, k, limit, block_sums, kcum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_register_docs(const uint32_t *doc_ids, uint64_t n, const uint32_t *phi,
+                                 uint32_t K, uint32_t R, uint32_t B, uint32_t W, uint32_t *docbits,
+                                 uint32_t *err, cudaStream_t s) {
+    const uint64_t total = n * R;
+    if (total == 0) return cudaSuccess;
+    k_register<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(doc_ids, n, phi, K, R, B, W, docbits,
+                                                               err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s) {
+    switch (a.eta) {
+        case 1: return launch_insert_t<1>(a, sm_count, s);
+        case 2: return launch_insert_t<2>(a, sm_count, s);
+        case 3: return launch_insert_t<3>(a, sm_count, s);
+        default: return launch_insert_t<4>(a, sm_count, s);
+    }
+}
+
+}  // namespace rgpu

@@ -1,0 +1,283 @@
+"""Python binding of librambo_gpu.so (the C ABI in include/rambo.h).
+
+Argument marshalling only: every step of insertion and query runs in the
+library's CUDA kernels.  Host-buffer calls take numpy arrays; device calls
+take torch CUDA tensors (PyTorch supplies device memory and streams).  There
+is no CPU fallback: if the library cannot be built or loaded, importing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+RAMBO_OK = 0
+RAMBO_EINVAL = -1
+RAMBO_ENOMEM = -2
+RAMBO_ECUDA = -3
+RAMBO_ERANGE = -4
+RAMBO_ETIMEOUT = -5
+RAMBO_ESTATE = -6
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RamboError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {code} ({_strerror(code)})")
+
+
+class _Info(C.Structure):
+    _fields_ = [("K", C.c_uint32), ("B", C.c_uint32), ("R", C.c_uint32), ("eta", C.c_uint32),
+                ("k", C.c_uint32), ("m", C.c_uint64), ("seed", C.c_uint64),
+                ("mask_words", C.c_uint32), ("group_bytes", C.c_uint32),
+                ("index_bytes", C.c_uint64), ("docbits_bytes", C.c_uint64), ("device", C.c_int)]
+
+
+def load():
+    """Builds (if stale) and loads the CUDA library; raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = C.CDLL(path)
+        u32, u64, p, i = C.c_uint32, C.c_uint64, C.c_void_p, C.c_int
+        sz = C.c_size_t
+        sig = {
+            "rambo_create": (i, [u32, u32, u32, u64, u32, u32, u64, i, C.POINTER(p)]),
+            "rambo_destroy": (i, [p]),
+            "rambo_mask_words": (u32, [p]),
+            "rambo_get_info": (i, [p, C.POINTER(_Info)]),
+            "rambo_strerror": (C.c_char_p, [i]),
+            "rambo_insert": (i, [p, u32, p, u64]),
+            "rambo_insert_batch": (i, [p, u32, p, p, p]),
+            "rambo_query_kmers": (i, [p, u64, p, p]),
+            "rambo_query_seqs": (i, [p, u64, p, p, p]),
+            "rambo_insert_workspace": (sz, [p, u64]),
+            "rambo_query_kmers_workspace": (sz, [p, u64]),
+            "rambo_query_seqs_workspace": (sz, [p, u64]),
+            "rambo_insert_batch_dev": (i, [p, u32, p, p, u64, p, p, sz, p]),
+            "rambo_query_kmers_dev": (i, [p, u64, p, p, p, sz, p]),
+            "rambo_query_seqs_dev": (i, [p, u64, p, u64, p, p, p, sz, p]),
+            "rambo_sync": (i, [p, p]),
+            "rambo_copy_index": (i, [p, u64, u64, p]),
+            "rambo_copy_docbits": (i, [p, p]),
+            "rambo_copy_partition": (i, [p, p]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load().rambo_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def _check(rc: int, what: str):
+    if rc != RAMBO_OK:
+        raise RamboError(rc, what)
+
+
+def _check_span(packed: np.ndarray, offs: np.ndarray):
+    """The host calls read the bytes holding bases [offs[0], offs[-1])."""
+    if offs.size and offs[-1] >= offs[0] and packed.size * 4 < int(offs[-1]):
+        raise ValueError("packed buffer is shorter than the bases the offsets address")
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data if a.size else None
+
+
+def _t_ptr(t):
+    return t.data_ptr() if t.numel() else None
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Workspace:
+    """A 256-byte aligned device buffer owned by torch, grown on demand."""
+
+    def __init__(self, device):
+        self.device = device
+        self._buf = None
+        self.ptr = 0
+        self.nbytes = 0
+
+    def get(self, nbytes: int) -> tuple[int, int]:
+        import torch
+        if nbytes > self.nbytes:
+            want = max(nbytes, 256) + nbytes // 4
+            self._buf = torch.empty(want + 256, dtype=torch.uint8, device=self.device)
+            base = self._buf.data_ptr()
+            self.ptr = (base + 255) // 256 * 256
+            self.nbytes = want
+        return self.ptr, self.nbytes
+
+
+class Index:
+    """One RAMBO index resident on a GPU (Section 3: R x B merged BFUs)."""
+
+    def __init__(self, K: int, B: int, R: int, m: int, eta: int, k: int = 31, seed: int = 0,
+                 device: int | None = None):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.rambo_create(K, B, R, m, eta, k, seed, -1 if device is None else device,
+                                C.byref(h)), "rambo_create")
+        self._h = h
+        info = _Info()
+        _check(lib.rambo_get_info(h, C.byref(info)), "rambo_get_info")
+        self.info = {f: getattr(info, f) for f, _ in _Info._fields_}
+        self.K, self.B, self.R, self.m, self.eta, self.k, self.seed = K, B, R, m, eta, k, seed
+        self.W = info.mask_words
+        self.device = info.device
+        self._ws = {}
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rambo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------- host buffers
+    def insert(self, doc_id: int, packed: np.ndarray, n_bases: int):
+        packed = np.ascontiguousarray(packed, dtype=np.uint8)
+        _check_span(packed, np.array([0, n_bases], dtype=np.uint64))
+        _check(load().rambo_insert(self._h, doc_id, _np_ptr(packed), n_bases), "rambo_insert")
+
+    def insert_batch(self, doc_ids, packed, offsets):
+        ids = np.ascontiguousarray(doc_ids, dtype=np.uint32)
+        packed = np.ascontiguousarray(packed, dtype=np.uint8)
+        offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+        if offs.size != ids.size + 1:
+            raise ValueError("offsets must have n_docs + 1 entries")
+        _check_span(packed, offs)
+        _check(load().rambo_insert_batch(self._h, ids.size, _np_ptr(ids), _np_ptr(packed),
+                                         _np_ptr(offs)), "rambo_insert_batch")
+
+    def query_kmers(self, kmers) -> np.ndarray:
+        km = np.ascontiguousarray(kmers, dtype=np.uint64)
+        out = np.zeros((km.size, self.W), dtype=np.uint32)
+        _check(load().rambo_query_kmers(self._h, km.size, _np_ptr(km), _np_ptr(out)),
+               "rambo_query_kmers")
+        return out
+
+    def query_seqs(self, packed, offsets) -> np.ndarray:
+        packed = np.ascontiguousarray(packed, dtype=np.uint8)
+        offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+        _check_span(packed, offs)
+        n = max(offs.size - 1, 0)
+        out = np.zeros((n, self.W), dtype=np.uint32)
+        _check(load().rambo_query_seqs(self._h, n, _np_ptr(packed), _np_ptr(offs), _np_ptr(out)),
+               "rambo_query_seqs")
+        return out
+
+    # ----------------------------------------------------- device buffers
+    def _workspace(self, stream_key, nbytes):
+        ws = self._ws.get(stream_key)
+        if ws is None:
+            ws = self._ws[stream_key] = Workspace(f"cuda:{self.device}")
+        return ws.get(nbytes)
+
+    def workspace_bytes(self, kind: str, n: int) -> int:
+        f = {"insert": "rambo_insert_workspace", "kmers": "rambo_query_kmers_workspace",
+             "seqs": "rambo_query_seqs_workspace"}[kind]
+        return int(getattr(load(), f)(self._h, n))
+
+    def insert_batch_dev(self, doc_ids, packed, offsets, stream=None, workspace=None):
+        """doc_ids int32/uint32, packed uint8, offsets int64 (n+1) CUDA tensors."""
+        n = doc_ids.numel()
+        need = self.workspace_bytes("insert", n)
+        s = _stream_handle(stream)
+        wp, wn = workspace if workspace is not None else self._workspace(s, need)
+        _check(load().rambo_insert_batch_dev(self._h, n, _t_ptr(doc_ids), _t_ptr(packed),
+                                             packed.numel(), _t_ptr(offsets), wp, wn, s),
+               "rambo_insert_batch_dev")
+
+    def query_kmers_dev(self, kmers, out=None, stream=None, workspace=None):
+        """kmers int64 CUDA tensor of forward codes; returns (n, W) int32 masks."""
+        import torch
+        n = kmers.numel()
+        if out is None:
+            out = torch.empty((n, self.W), dtype=torch.int32, device=kmers.device)
+        need = self.workspace_bytes("kmers", n)
+        s = _stream_handle(stream)
+        wp, wn = workspace if workspace is not None else self._workspace(s, need)
+        _check(load().rambo_query_kmers_dev(self._h, n, _t_ptr(kmers), _t_ptr(out), wp, wn, s),
+               "rambo_query_kmers_dev")
+        return out
+
+    def query_seqs_dev(self, packed, offsets, out=None, stream=None, workspace=None):
+        """packed uint8 and offsets int64 (n+1) CUDA tensors; returns (n, W) int32."""
+        import torch
+        n = offsets.numel() - 1
+        if out is None:
+            out = torch.empty((max(n, 0), self.W), dtype=torch.int32, device=offsets.device)
+        need = self.workspace_bytes("seqs", max(n, 0))
+        s = _stream_handle(stream)
+        wp, wn = workspace if workspace is not None else self._workspace(s, need)
+        _check(load().rambo_query_seqs_dev(self._h, max(n, 0), _t_ptr(packed), packed.numel(),
+                                           _t_ptr(offsets), _t_ptr(out), wp, wn, s),
+               "rambo_query_seqs_dev")
+        return out
+
+    def sync(self, stream=None):
+        _check(load().rambo_sync(self._h, _stream_handle(stream)), "rambo_sync")
+
+    # ------------------------------------------------------ introspection
+    def copy_index(self, offset: int = 0, nbytes: int | None = None) -> np.ndarray:
+        total = self.info["index_bytes"]
+        if nbytes is None:
+            nbytes = total - offset
+        out = np.zeros(nbytes, dtype=np.uint8)
+        _check(load().rambo_copy_index(self._h, offset, nbytes, _np_ptr(out)), "rambo_copy_index")
+        return out
+
+    def docbits(self) -> np.ndarray:
+        out = np.zeros((self.R, self.B, self.W), dtype=np.uint32)
+        _check(load().rambo_copy_docbits(self._h, _np_ptr(out)), "rambo_copy_docbits")
+        return out
+
+    def partition(self) -> np.ndarray:
+        out = np.zeros((self.K, self.R), dtype=np.uint32)
+        _check(load().rambo_copy_partition(self._h, _np_ptr(out)), "rambo_copy_partition")
+        return out
+
+
+def as_u32(t) -> np.ndarray:
+    """A (n, W) int32 torch mask tensor as a host uint32 array."""
+    return t.cpu().numpy().view(np.uint32)

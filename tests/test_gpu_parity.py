@@ -1,0 +1,238 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every result here is integer/bit work, so the bar is equality: answer masks,
+index bits, bucket->document bitmaps and partitions must match the oracle
+exactly on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_04358_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(a, dtype):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a).view(dtype)).cuda()
+
+
+def gpu_index(rambo, p, corpus, via="dev", chunks=1):
+    idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    n = corpus.doc_ids.size
+    bounds = np.linspace(0, n, chunks + 1).astype(int)
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        if b <= a:
+            continue
+        ids = corpus.doc_ids[a:b]
+        offs = corpus.offsets[a:b + 1]
+        if via == "dev":
+            torch = _torch()
+            idx.insert_batch_dev(_dev(ids.astype(np.uint32), np.int32),
+                                 _dev(corpus.packed, np.uint8),
+                                 _dev(offs.astype(np.uint64), np.int64))
+            idx.sync()
+        else:
+            idx.insert_batch(ids, corpus.packed, offs)
+    return idx
+
+
+def oracle_index(p, corpus, threads=4):
+    o = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    o.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets, threads=threads)
+    return o
+
+
+def gpu_query_seqs(rambo, idx, q_packed, q_offsets):
+    out = idx.query_seqs_dev(_dev(q_packed, np.uint8), _dev(q_offsets.astype(np.uint64), np.int64))
+    idx.sync()
+    return rambo.as_u32(out)
+
+
+def assert_index_equal(idx, o, p):
+    """GPU bit-sliced groups vs the oracle's separate filters, bit for bit."""
+    G = idx.info["group_bytes"]
+    words = idx.copy_index().view(np.uint32).reshape(p.m, G // 4)
+    for r in range(p.R):
+        for b in range(p.B):
+            i = r * p.B + b
+            gpu_bits = ((words[:, i >> 5] >> np.uint32(i & 31)) & 1).astype(np.uint8)
+            fw = o.filter_words(r, b)
+            orc_bits = np.unpackbits(fw.view(np.uint8), bitorder="little")[:p.m]
+            assert np.array_equal(gpu_bits, orc_bits), f"BFU ({b},{r}) differs"
+    # padding bits of every group stay zero
+    used = p.R * p.B
+    for w in range(G // 4):
+        lo = w * 32
+        if lo >= used:
+            assert not words[:, w].any()
+        elif lo + 32 > used:
+            assert not (words[:, w] >> np.uint32(used - lo)).any()
+
+
+def assert_docbits_equal(idx, o, p):
+    db = idx.docbits()
+    part = idx.partition()
+    for d in range(p.K):
+        for r in range(p.R):
+            assert part[d, r] == o.bucket(d, r)
+    for r in range(p.R):
+        for b in range(p.B):
+            docs = oracle.mask_to_docs(db[r, b])
+            want = {d for d in range(p.K) if o.is_inserted(d) and o.bucket(d, r) == b}
+            assert docs == want
+
+
+# ------------------------------------------------------------------ tiny
+
+@pytest.fixture(scope="module")
+def tiny():
+    corpus, q = synth.tiny_workload()
+    p = corpus.params
+    return p, corpus, q, oracle_index(p, corpus)
+
+
+def test_tiny_index_bits_match_oracle(rambo_lib, tiny):
+    p, corpus, q, o = tiny
+    idx = gpu_index(rambo_lib, p, corpus)
+    assert_index_equal(idx, o, p)
+    assert_docbits_equal(idx, o, p)
+
+
+def test_tiny_sequence_queries_match_oracle(rambo_lib, tiny):
+    p, corpus, q, o = tiny
+    idx = gpu_index(rambo_lib, p, corpus)
+    want = o.query_seqs(q.packed, q.offsets)
+    got = gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets)
+    assert np.array_equal(got, want)
+    # the host-buffer entry point gives the same bits
+    assert np.array_equal(idx.query_seqs(q.packed, q.offsets), want)
+
+
+def test_tiny_kmer_queries_match_oracle(rambo_lib, tiny):
+    p, corpus, q, o = tiny
+    idx = gpu_index(rambo_lib, p, corpus, via="host")
+    rng = np.random.default_rng(5)
+    kmers = synth.sample_kmers(rng, corpus, 3000, p.k, 0.5)
+    want = o.query_kmers(kmers)
+    assert np.array_equal(idx.query_kmers(kmers), want)
+    got = idx.query_kmers_dev(_dev(kmers, np.int64))
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(got), want)
+
+
+# --------------------------------------------------------- parameter sweep
+
+SWEEP = [
+    # K,    B,   R,  m,          eta, k   -> group bytes
+    (37, 3, 1, 1 << 12, 1, 11),      # 4
+    (64, 10, 3, 5003, 2, 15),        # 4, m not a power of two
+    (100, 16, 4, 1 << 14, 3, 31),    # 8
+    (33, 32, 4, 1 << 13, 2, 31),     # 16
+    (200, 30, 2, 1 << 13, 4, 21),    # 8
+    (150, 50, 3, 1 << 12, 2, 31),    # 32
+    (300, 100, 5, 1 << 13, 2, 31),   # 64
+    (500, 64, 6, 12289, 5, 25),      # 64, eta > 4 (probe passes), odd m
+    (700, 316, 6, 1 << 12, 2, 31),   # 256
+    (90, 700, 3, 1 << 11, 2, 32),    # 512? 2100 bits -> 512 B, k = 32
+    (60, 1500, 3, 1 << 10, 3, 31),   # 1024 bytes: two chunks
+    (5, 1, 1, 1 << 10, 2, 9),        # B = R = 1
+    (1, 4, 2, 1 << 10, 2, 7),        # K = 1
+]
+
+
+@pytest.mark.parametrize("K,B,R,m,eta,k", SWEEP)
+def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k):
+    p = synth.Params(K=K, B=B, R=R, m=m, eta=eta, k=k, seed=K + B)
+    rng = np.random.default_rng(K * 7 + B)
+    corpus = synth.family_corpus(rng, p, n_seeds=max(1, K // 8), doc_len=400, sub_rate=0.02)
+    q = synth.sample_queries(rng, corpus, rng.integers(max(1, k - 3), 200, size=300), 0.6)
+    o = oracle_index(p, corpus)
+    idx = gpu_index(rambo_lib, p, corpus, chunks=3)
+    assert_index_equal(idx, o, p)
+    assert_docbits_equal(idx, o, p)
+    assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets),
+                          o.query_seqs(q.packed, q.offsets))
+    kmers = synth.sample_kmers(rng, corpus, 500, k, 0.5)
+    assert np.array_equal(idx.query_kmers(kmers), o.query_kmers(kmers))
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_edge_cases(rambo_lib):
+    p = synth.Params(K=45, B=7, R=3, m=1 << 12, eta=2, k=31, seed=9)
+    rng = np.random.default_rng(3)
+    lens = [0, 5, 30, 31, 32, 200, 31, 0, 1000]
+    docs = [synth.uniform_genome(rng, L) for L in lens]
+    packed, offs = synth.pack_many(docs)
+    ids = np.array([0, 1, 2, 3, 4, 5, 44, 6, 7], dtype=np.uint32)
+    corpus = synth.Corpus(p, ids, packed, offs)
+    o = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    o.insert_batch(ids, packed, offs)
+    idx = rambo_lib.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    idx.insert_batch(ids, packed, offs)
+    # duplicate insert of the whole batch is idempotent
+    idx.insert_batch(ids, packed, offs)
+    assert_index_equal(idx, o, p)
+    assert_docbits_equal(idx, o, p)
+    # queries: empty, shorter than k, exactly k, ragged, from the documents
+    qs = [np.zeros(0, np.uint8), docs[1][:5], docs[4][:31], docs[5][17:150], docs[8][3:900],
+          docs[3], synth.uniform_genome(rng, 31), docs[8]]
+    qp, qo = synth.pack_many(qs)
+    want = o.query_seqs(qp, qo)
+    got = gpu_query_seqs(rambo_lib, idx, qp, qo)
+    assert np.array_equal(got, want)
+    inserted = {int(d) for d in ids}
+    assert oracle.mask_to_docs(got[0]) == inserted  # no term: every inserted document
+    assert oracle.mask_to_docs(got[1]) == inserted
+    # an empty batch is a no-op
+    assert idx.query_seqs(qp[:0], np.zeros(1, np.uint64)).shape == (0, idx.W)
+    # misaligned device pointers: the same bytes seen through an odd offset
+    torch = _torch()
+    qp_pad = np.concatenate([np.zeros(3, np.uint8), qp])
+    t = _dev(qp_pad, np.uint8)[3:]
+    out = idx.query_seqs_dev(t, _dev(qo.astype(np.uint64), np.int64))
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(out), want)
+    # offsets not starting at zero
+    shifted = np.concatenate([np.zeros(1, np.uint64), qo + np.uint64(4)])
+    qp2 = np.concatenate([np.zeros(1, np.uint8), qp])
+    got2 = idx.query_seqs(qp2, shifted[1:])
+    assert np.array_equal(got2, want)
+
+
+def test_argument_errors(rambo_lib):
+    with pytest.raises(rambo_lib.RamboError):
+        rambo_lib.Index(0, 1, 1, 64, 1)
+    with pytest.raises(rambo_lib.RamboError):
+        rambo_lib.Index(4, 2, 1, 64, 0)
+    with pytest.raises(rambo_lib.RamboError):
+        rambo_lib.Index(4, 2, 1, (1 << 32) + 1, 1)
+    idx = rambo_lib.Index(10, 2, 2, 1 << 10, 2, k=31)
+    packed, offs = synth.pack_many([np.zeros(40, np.uint8)])
+    with pytest.raises(rambo_lib.RamboError) as e:
+        idx.insert_batch(np.array([10], np.uint32), packed, offs)
+    assert e.value.code == rambo_lib.RAMBO_ERANGE
+    with pytest.raises(rambo_lib.RamboError) as e:
+        idx.query_kmers(np.array([1 << 62], np.uint64))
+    assert e.value.code == rambo_lib.RAMBO_EINVAL
+    with pytest.raises(rambo_lib.RamboError) as e:
+        idx.query_seqs(packed, np.array([5, 3], np.uint64))
+    assert e.value.code == rambo_lib.RAMBO_EINVAL
+    # device-side checks latch an error reported by sync, and skip the item
+    idx.insert_batch_dev(_dev(np.array([3, 11], np.uint32), np.int32), _dev(packed, np.uint8),
+                         _dev(np.array([0, 20, 40], np.uint64), np.int64))
+    with pytest.raises(rambo_lib.RamboError) as e:
+        idx.sync()
+    assert e.value.code == rambo_lib.RAMBO_ERANGE
+    idx.sync()  # cleared
+    idx.query_kmers_dev(_dev(np.array([1 << 62, 5], np.uint64), np.int64))
+    with pytest.raises(rambo_lib.RamboError) as e:
+        idx.sync()
+    assert e.value.code == rambo_lib.RAMBO_EINVAL
