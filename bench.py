@@ -1,0 +1,483 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched RAMBO query on one GB300.
+
+One step = one pass of the whole query path (k-mer extraction, hashing,
+probing, bucket-space AND, expansion to document masks) over one batch:
+the medium workload's 10^6 single 31-mers plus 10^4 sequences of 1 kbp,
+against an index of 1,000 documents x 1 Mbp (R=4, B=32, m=2^26, eta=2).
+The index is built once before timing (build throughput is reported beside
+the query numbers).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload medium|large|tiny]
+
+--impl reference times the CPU oracle (plain single-pass RAMBO in C) on the
+host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "k-mer queries/s and query bp/s on 1 GB300 (bit-exact vs oracle); serving p50/p99 ms"
+UNIT = "k-mer queries/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+PROBE_SRC = os.path.join(ROOT, "paper_1910_04358_gb300", "csrc", "rambo_kernels_query.cu")
+SECTOR = 32
+STAGES_ALL = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# workloads
+
+
+def load_workload(name: str):
+    from paper_1910_04358_gb300 import synth
+    if name == "medium":
+        corpus, kmers, q = synth.medium_workload()
+        desc = ("1,000 docs x 1 Mbp (20 seed genomes, 1% substitutions); R=4 B=32 m=2^26 eta=2 k=31; "
+                "batch = 10^6 single 31-mers (50% present) + 10^4 x 1 kbp sequences (50% from docs)")
+    elif name == "large":
+        corpus, q = synth.large_workload()
+        kmers = np.zeros(0, np.uint64)
+        desc = ("10,000 docs x 500 kbp (200 seeds, 0.5% subs, 0.05% indels); R=5 B=100 m=2^29 eta=2 "
+                "k=31; batch = 10^5 sequences of U[31,5000] bp, 70% from docs with 0.1% errors")
+    elif name == "tiny":
+        corpus, q = synth.tiny_workload()
+        kmers = np.zeros(0, np.uint64)
+        desc = "100 docs x 20 kbp; R=2 B=10 m=2^20 eta=2; batch = 1,000 x 100 bp"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return corpus, kmers, q, desc
+
+
+def batch_stats(p, kmers, q):
+    n_seq_kmers = q.n_kmers(p.k)
+    total_kmers = int(kmers.size) + n_seq_kmers
+    bp = int(kmers.size) * p.k + q.n_bases
+    return n_seq_kmers, total_kmers, bp
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []  # (t, sm, max, reasons)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        threading.Thread(target=self._reader, daemon=True).start()
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm, mx = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = [n for n, v in zip(names, parts[5:9]) if v.lower() == "active"]
+            self.samples.append((time.time(), sm, mx, reasons))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        window = "timed region"
+        if len(inside) < 3:  # short timed region: widen to the surrounding loaded window
+            inside = [s for s in self.samples if t0 - 1.0 <= s[0] <= t1 + 0.3]
+            window = "timed region +-1 s"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "window": "no samples"}
+        reasons = sorted({r for s in inside for r in s[3]})
+        return {"sm_mhz": statistics.median(s[1] for s in inside),
+                "sm_max_mhz": max(s[2] for s in inside), "reasons": reasons,
+                "samples": len(inside), "window": window}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+
+
+def measured_peak_gbs():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def probe_bytes_per_kmer(info) -> int:
+    """eta position groups per k-mer, each rounded up to whole 32-byte sectors."""
+    g = info["group_bytes"]
+    return info["eta"] * SECTOR * ((g + SECTOR - 1) // SECTOR)
+
+
+def probe_algorithmic_bytes(info, n_kmers: int, n_queries: int, n_bases: int) -> int:
+    """Bytes the probe kernel must move: the index sectors of every probe, the
+    packed input (1/4 byte per base), offsets and k-mer prefix (16 B/query)
+    and the per-query bucket-mask write (group bytes per query)."""
+    return (n_kmers * probe_bytes_per_kmer(info) + n_bases // 4 + 16 * n_queries
+            + n_queries * info["group_bytes"])
+
+
+def source_digest(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(workload: str, kernel: str):
+    """dram bytes per launch from a committed ncu capture, if the kernel source
+    has not changed since the counters were taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        e = t[workload][kernel]
+        if e.get("source_sha") != source_digest(PROBE_SRC):
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (independent replicas; no data-path collective)
+
+
+def dist_setup(backend: str):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+
+
+def oracle_sample(p, corpus, kmers, q, frac_kmers: int, frac_seqs: int, threads: int):
+    """Restricted-mode oracle for a sample of the batch: tracks only the probe
+    positions the sample touches (exact for those queries)."""
+    import oracle
+    ks = kmers[::frac_kmers] if kmers.size else kmers
+    sel = np.arange(0, q.n, frac_seqs)
+    offs = q.offsets.astype(np.int64)
+    seq_offs = np.concatenate([[0], np.cumsum(offs[sel + 1] - offs[sel])]).astype(np.uint64)
+    # gather the sampled sequences into one packed stream
+    from paper_1910_04358_gb300 import synth
+    stream = synth.PackedStream()
+    for i in sel:
+        stream.append(synth.unpack_bases(q.packed, int(offs[i]), int(offs[i + 1] - offs[i])))
+    s_packed, s_offs = stream.finish()
+    probe = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, tracked=[0])
+    pos = set()
+    for x in ks.tolist():
+        c = oracle.canonical_of_code(int(x), p.k)
+        pos.update(probe.probe_position(c, j) for j in range(p.eta))
+    for i in range(s_offs.size - 1):
+        for t in range(int(s_offs[i]), int(s_offs[i + 1]) - p.k + 1):
+            c = oracle.kmer_canonical(s_packed, t, p.k)
+            pos.update(probe.probe_position(c, j) for j in range(p.eta))
+    probe.close()
+    o = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, tracked=sorted(pos))
+    t0 = time.time()
+    o.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets, threads=threads)
+    build_s = time.time() - t0
+    return o, ks, s_packed, s_offs, build_s
+
+
+def time_oracle(o, ks, s_packed, s_offs, threads: int):
+    t0 = time.perf_counter()
+    if ks.size:
+        o.query_kmers(ks, threads=threads)
+    if s_offs.size > 1:
+        o.query_seqs(s_packed, s_offs, threads=threads)
+    return time.perf_counter() - t0
+
+
+def sample_kmers_count(p, ks, s_offs):
+    L = np.diff(s_offs.astype(np.int64))
+    return int(ks.size) + int(np.maximum(L - p.k + 1, 0).sum())
+
+
+def run_reference(args):
+    rank, local, world = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    corpus, kmers, q, desc = load_workload(args.workload)
+    p = corpus.params
+    threads = os.cpu_count() or 1
+    fk, fs = (200, 100) if args.workload == "medium" else (1, 50)
+    log(f"[reference] building restricted-mode oracle index on {threads} threads")
+    o, ks, sp, so, build_s = oracle_sample(p, corpus, kmers, q, fk, fs, threads)
+    units = sample_kmers_count(p, ks, so)
+    bp = int(ks.size) * p.k + int(so[-1])
+    for _ in range(args.warmup):
+        time_oracle(o, ks, sp, so, threads)
+    times = [time_oracle(o, ks, sp, so, threads) for _ in range(args.steps)]
+    total = sum(times)
+    value = units * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded)",
+        "config": {"workload": args.workload, "desc": desc, "sample": f"1/{fk} of k-mers, 1/{fs} of sequences"},
+        "query_bp_per_s": bp * len(times) / total,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{ks.size} k-mers + {so.size - 1} sequences per step "
+                                   f"({units} k-mers), restricted-mode index built in {build_s:.1f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+
+def run_ours(args):
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_1910_04358_gb300 import rambo
+
+    corpus, kmers, q, desc = load_workload(args.workload)
+    p = corpus.params
+    n_seq_kmers, total_kmers, bp = batch_stats(p, kmers, q)
+
+    def to_dev(a, dt):
+        return torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
+
+    idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=local)
+    info = idx.info
+    # ---- build (Algorithm 1), timed separately
+    d_ids, d_cp, d_co = to_dev(corpus.doc_ids, np.int32), to_dev(corpus.packed, np.uint8), \
+        to_dev(corpus.offsets, np.int64)
+    torch.cuda.synchronize()
+    idx.profile_reset(timed_stages=("insert",))
+    t0 = time.perf_counter()
+    idx.insert_batch_dev(d_ids, d_cp, d_co)
+    idx.sync()
+    build_s = time.perf_counter() - t0
+    prof_b = idx.profile_read()
+    insert_kmers = int(np.maximum(np.diff(corpus.offsets.astype(np.int64)) - p.k + 1, 0).sum())
+    del d_cp
+    torch.cuda.empty_cache()
+
+    # ---- query batch resident in HBM
+    d_k = to_dev(kmers, np.int64) if kmers.size else None
+    d_qp, d_qo = to_dev(q.packed, np.uint8), to_dev(q.offsets, np.int64)
+    out_k = torch.empty((kmers.size, idx.W), dtype=torch.int32, device=dev) if kmers.size else None
+    out_s = torch.empty((q.n, idx.W), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if d_k is not None:
+            idx.query_kmers_dev(d_k, out=out_k)
+        idx.query_seqs_dev(d_qp, d_qo, out=out_s)
+
+    for _ in range(args.warmup):
+        step()
+    idx.sync()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    idx.profile_reset(timed_stages=("probe_seqs", "probe_kmers"))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(world)
+    idx.sync()
+    time.sleep(0.2)
+    clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world, dev)
+    ms_step = ms_total / args.steps
+    prof = idx.profile_read()
+    launches = sum(v["launches"] for v in prof.values())
+    # per-stage breakdown from a separate profiled pass (every stage bracketed)
+    idx.profile_reset(timed_stages=STAGES_ALL)
+    for _ in range(min(args.steps, 20)):
+        step()
+    idx.sync()
+    prof_all = idx.profile_read()
+
+    value = total_kmers * world / (ms_step / 1e3)
+    bp_s = bp * world / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel (sequence probe)
+    dom = "probe_seqs" if q.n else "probe_kmers"
+    dom_ms = prof[dom]["ms"] / max(prof[dom]["timed"], 1)
+    alg_bytes = probe_algorithmic_bytes(info, n_seq_kmers, q.n, q.n_bases)
+    peak, peak_src = measured_peak_gbs()
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    traffic = measured_traffic(args.workload, dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": f"k_probe_seqs",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_per_kmer": probe_bytes_per_kmer(info), "avg_launch_ms": dom_ms,
+                "peak_source": peak_src}
+    kernel_ms = {k: (v["ms"] / (min(args.steps, 20)) if v["timed"] else None)
+                 for k, v in prof_all.items()}
+
+    # ---- correctness spot check of the timed outputs against the host path
+    spot = min(q.n, 64)
+    host_chk = idx.query_seqs(q.packed, q.offsets[:spot + 1])
+    ok = bool(np.array_equal(rambo.as_u32(out_s[:spot]), host_chk))
+
+    # ---- end to end through the host-buffer C ABI (H2D + D2H inside)
+    e2e = None
+    if not args.no_e2e:
+        pin_k = torch.from_numpy(kmers.view(np.int64)).pin_memory().numpy().view(np.uint64) \
+            if kmers.size else kmers
+        pin_p = torch.from_numpy(q.packed).pin_memory().numpy()
+        pin_o = torch.from_numpy(q.offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        e2e_steps = max(3, min(args.steps, 30))
+        for _ in range(2):
+            if kmers.size:
+                idx.query_kmers(pin_k)
+            idx.query_seqs(pin_p, pin_o)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            if kmers.size:
+                idx.query_kmers(pin_k)
+            idx.query_seqs(pin_p, pin_o)
+        t_e2e = (time.perf_counter() - t0) / e2e_steps
+        t_e2e = max_over_ranks(t_e2e, world, dev)
+        h2d = int(kmers.nbytes) + int(q.packed.nbytes) + int(q.offsets.nbytes)
+        d2h = (int(kmers.size) + q.n) * idx.W * 4
+        e2e = {"value": total_kmers * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e, "steps": e2e_steps}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        fk, fs = (200, 100) if args.workload == "medium" else (1, 50)
+        o, ks, sp, so, obuild = oracle_sample(p, corpus, kmers, q, fk, fs, threads)
+        units = sample_kmers_count(p, ks, so)
+        reps, spent = 0, 0.0
+        while spent < 10.0 and reps < 200:
+            spent += time_oracle(o, ks, sp, so, threads)
+            reps += 1
+        cpu = {"value": units * reps / spent, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{ks.size} single k-mers + {so.size - 1} sequences ({units} k-mers) "
+                         f"x {reps} repetitions; restricted-mode oracle index "
+                         f"(tracks the sample's probe positions), built in {obuild:.1f} s"}
+
+    clk = clocks.summary(t_wall0, t_wall1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+        "config": {"workload": args.workload, "desc": desc,
+                   "l2": "inputs larger than L2: index %.2f GB probed at random" % (info["index_bytes"] / 1e9),
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "query_bp_per_s": bp_s, "kmers_per_step": total_kmers, "bp_per_step": bp,
+        "gpu_launches": launches, "roofline": roofline, "stage_ms_per_step": kernel_ms,
+        "build": {"seconds": build_s, "kmers": insert_kmers, "kmers_per_s": insert_kmers / build_s,
+                  "insert_kernel_ms": prof_b["insert"]["ms"] or None},
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "spot_check_vs_host_api": ok,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0 if ok else 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["medium", "large", "tiny"], default="medium")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

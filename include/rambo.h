@@ -19,8 +19,9 @@
  *  Sequences   2-bit packed: base t of a buffer is in byte t>>2 at bits
  *              2*(t&3)..2*(t&3)+1; A=0, C=1, G=2, T=3.  A batch is one packed
  *              buffer plus CSR base offsets (n+1 uint64): item i is bases
- *              [offsets[i], offsets[i+1]).  Offsets may start anywhere and
- *              items may overlap.
+ *              [offsets[i], offsets[i+1]).  Offsets may start at any base;
+ *              host calls read every byte holding bases [offsets[0],
+ *              offsets[n]), device calls read at most `packed_bytes` bytes.
  *  Terms       canonical k-mers: min(forward code, reverse-complement code),
  *              forward code = first base most significant (Section 3.3.1,
  *              Section 5.1 "2-bit encoding"; canonical form is this library's
@@ -184,6 +185,65 @@ int rambo_copy_docbits(const rambo_t *h, uint32_t *dst);
 
 /* Copies phi: dst[d*R + r] = bucket of document d in repetition r. */
 int rambo_copy_partition(const rambo_t *h, uint32_t *dst);
+
+/* ---------------------------------------------------------------------- */
+/* Tuning knobs (launch shapes; none changes any result).                  */
+
+typedef struct {
+    uint32_t probe_ctas_per_sm;        /* probe grid = SMs x this; 0 = occupancy max */
+    uint32_t probe_min_kmers_per_warp; /* smallest k-mer range a warp takes; 0 = 64  */
+    uint32_t expand_ctas_per_sm;       /* expansion grid cap = SMs x this (1..64)    */
+    uint32_t use_byte_table;           /* 1: expand through a per-8-bucket OR table  */
+    uint32_t byte_table_max_mb;        /* ... only if it fits this many MiB          */
+} rambo_tuning_t;
+
+int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out);
+/* Applies new knobs after waiting for the handle's stream; RAMBO_EINVAL if a
+ * knob is out of range.  Results are bit-identical for every setting. */
+int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement support (not part of the paper).                            */
+
+/* Random-record gather on the current device: n_probes reads of
+ * record_bytes (16..512, power of two) at pseudo-random record indices of
+ * `buf` (device, 16-byte aligned, buf_bytes long), with load instruction
+ * variant 0..5 (0 = the probe kernels' streaming load).  XOR of the data goes
+ * to the 8-byte device word `sink`.  Asynchronous on `stream`. */
+int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t record_bytes,
+                       uint64_t n_probes, uint32_t load_variant, uint64_t seed, void *sink,
+                       void *stream);
+
+/* Reads (into *previous) and, if bytes > 0, sets the current context's L2
+ * fetch granularity limit (32, 64 or 128 bytes).  A per-process context
+ * limit; it ends with the process. */
+int rambo_set_l2_fetch_granularity(int bytes, int *previous);
+
+/* ---------------------------------------------------------------------- */
+/* Profiling.  The library counts every kernel it launches, per stage, and */
+/* can bracket the launches of selected stages with CUDA events recorded on */
+/* the launching stream.  (Not part of the paper: measurement support.)    */
+
+#define RAMBO_STAGE_PREFIX 0      /* k-mer count prefix scan (3 kernels)      */
+#define RAMBO_STAGE_REGISTER 1    /* bucket->document bitmap registration     */
+#define RAMBO_STAGE_INSERT 2      /* Algorithm 1 bit setting                  */
+#define RAMBO_STAGE_PROBE_SEQS 3  /* sequence probe + bucket-space AND        */
+#define RAMBO_STAGE_PROBE_KMERS 4 /* single k-mer probe                        */
+#define RAMBO_STAGE_EXPAND 5      /* union per repetition, AND over R          */
+#define RAMBO_NUM_STAGES 6
+
+typedef struct {
+    uint64_t launches[RAMBO_NUM_STAGES]; /* kernels launched since the last reset      */
+    uint64_t timed[RAMBO_NUM_STAGES];    /* launches bracketed by events                */
+    double ms[RAMBO_NUM_STAGES];         /* summed event time of the bracketed launches */
+} rambo_profile_t;
+
+/* Resets the counters and selects the stages whose launches are bracketed
+ * by events (bit s of stage_mask = stage s; 0 = counting only). */
+int rambo_profile_reset(rambo_t *h, uint32_t stage_mask);
+
+/* Waits for every recorded event, then copies the counters to *out. */
+int rambo_profile_read(rambo_t *h, rambo_profile_t *out);
 
 #ifdef __cplusplus
 }

@@ -192,9 +192,11 @@ typedef struct {
     /* R*B Bloom filters, filter (r,b) at index r*B+b, each nbits bits. */
     uint64_t **filter;
     uint64_t nbits;
-    /* Restricted mode: sorted distinct tracked positions (NULL = full). */
+    /* Restricted mode: sorted distinct tracked positions (NULL = full),
+     * plus an m-bit membership bitmap of them. */
     uint64_t *tracked;
     uint64_t n_tracked;
+    uint64_t *tracked_bits;
     /* DocIDs(M[b,r]) as growable lists; bucket[d*R + r] = phi_r(d). */
     uint32_t **docs;
     uint32_t *ndocs, *capdocs;
@@ -213,6 +215,7 @@ uint64_t orc_probe_position(const orc_rambo *o, uint64_t term, uint32_t j) {
 /* Position -> bit index inside a filter; -1 when restricted and untracked. */
 static int64_t orc_slot(const orc_rambo *o, uint64_t pos) {
     if (!o->tracked) return (int64_t)pos;
+    if (!((o->tracked_bits[pos >> 6] >> (pos & 63)) & 1)) return -1;
     uint64_t lo = 0, hi = o->n_tracked;
     while (lo < hi) {
         uint64_t mid = (lo + hi) / 2;
@@ -229,7 +232,7 @@ void orc_destroy(orc_rambo *o) {
     if (o->docs)
         for (uint64_t i = 0; i < (uint64_t)o->R * o->B; ++i) free(o->docs[i]);
     free(o->filter); free(o->docs); free(o->ndocs); free(o->capdocs);
-    free(o->bucket); free(o->inserted); free(o->tracked);
+    free(o->bucket); free(o->inserted); free(o->tracked); free(o->tracked_bits);
     free(o);
 }
 
@@ -248,6 +251,11 @@ static orc_rambo *orc_create_impl(uint32_t K, uint32_t B, uint32_t R, uint64_t m
         o->n_tracked = n_tracked;
         for (uint64_t i = 1; i < n_tracked; ++i)
             if (tracked[i] <= tracked[i - 1]) { orc_destroy(o); return NULL; }
+        if (n_tracked && tracked[n_tracked - 1] >= m) { orc_destroy(o); return NULL; }
+        o->tracked_bits = (uint64_t *)calloc((m + 63) / 64, sizeof(uint64_t));
+        if (!o->tracked_bits) { orc_destroy(o); return NULL; }
+        for (uint64_t i = 0; i < n_tracked; ++i)
+            o->tracked_bits[tracked[i] >> 6] |= (uint64_t)1 << (tracked[i] & 63);
         o->nbits = n_tracked;
     } else {
         o->nbits = m;
@@ -323,14 +331,16 @@ static void orc_insert_terms(orc_rambo *o, uint32_t d, const uint8_t *packed, ui
     uint8_t *bases = (uint8_t *)malloc(n_bases);
     if (!bases) return;
     orc_unpack(packed, begin, n_bases, bases);
+    int64_t slot[64];
     for (uint64_t s = 0; s + o->k <= n_bases; ++s) {
         uint64_t x = orc_canonical_of_window(bases + s, o->k);
+        /* Insert(x): the eta bit positions h_1(x)..h_eta(x) of a BFU */
+        for (uint32_t j = 0; j < o->eta; ++j) slot[j] = orc_slot(o, orc_probe_position(o, x, j));
+        /* ... set in BFU (phi_r(d), r) of every repetition r */
         for (uint32_t r = 0; r < o->R; ++r) {
             uint64_t f = (uint64_t)r * o->B + o->bucket[(uint64_t)d * o->R + r];
-            for (uint32_t j = 0; j < o->eta; ++j) {
-                int64_t slot = orc_slot(o, orc_probe_position(o, x, j));
-                if (slot >= 0) orc_set_bit(o->filter[f], (uint64_t)slot, atomic);
-            }
+            for (uint32_t j = 0; j < o->eta; ++j)
+                if (slot[j] >= 0) orc_set_bit(o->filter[f], (uint64_t)slot[j], atomic);
         }
     }
     free(bases);

@@ -3,6 +3,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "rambo.h"
 #include "rambo_internal.cuh"
@@ -20,6 +21,19 @@ struct rambo {
     uint32_t *d_err;         // latched device error bits
     void *d_stage;           // host-call staging + workspace
     size_t stage_bytes;
+    uint32_t *d_tab;         // byte table for the expansion (or null)
+    rambo_tuning_t tune;
+    // profiling
+    uint32_t prof_mask;
+    uint64_t launches[RAMBO_NUM_STAGES];
+    uint64_t timed[RAMBO_NUM_STAGES];
+    double ms[RAMBO_NUM_STAGES];
+    struct Pending {
+        int stage;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace rgpu {
@@ -86,6 +100,77 @@ int cuda_rc(cudaError_t e) {
         if (rc_ != RAMBO_OK) return rc_;        \
     } while (0)
 
+// Brackets the launches of one stage: counts them and, if the stage is
+// selected for timing, records events on the launching stream.
+class StageScope {
+  public:
+    StageScope(rambo_t *h, int stage, cudaStream_t s, int kernels) : h_(h), stage_(stage), s_(s) {
+        h_->launches[stage] += kernels;
+        if (!(h_->prof_mask & (1u << stage))) return;
+        start_ = take();
+        stop_ = take();
+        if (start_ && stop_ && cudaEventRecord(start_, s_) == cudaSuccess) armed_ = true;
+    }
+    ~StageScope() {
+        if (armed_ && cudaEventRecord(stop_, s_) == cudaSuccess) {
+            h_->pending.push_back({stage_, start_, stop_});
+        } else {
+            give(start_);
+            give(stop_);
+        }
+    }
+
+  private:
+    cudaEvent_t take() {
+        if (!h_->event_pool.empty()) {
+            cudaEvent_t e = h_->event_pool.back();
+            h_->event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    void give(cudaEvent_t e) {
+        if (e) h_->event_pool.push_back(e);
+    }
+    rambo_t *h_;
+    int stage_;
+    cudaStream_t s_;
+    cudaEvent_t start_ = nullptr, stop_ = nullptr;
+    bool armed_ = false;
+};
+
+// Probe grid: CTAs per SM from the tuning (0 = occupancy maximum).
+int probe_grid(const rambo_t *h) {
+    return h->tune.probe_ctas_per_sm ? -(int)(h->sm_count * h->tune.probe_ctas_per_sm) : h->sm_count;
+}
+
+// (Re)allocates or frees the byte table to match the tuning; the table is
+// rebuilt from the current bitmaps on the handle's stream.
+int apply_bytetab(rambo_t *h) {
+    const Geometry &g = h->g;
+    const uint64_t bytes = bytetab_words(g.B, g.R, g.W) * 4;
+    const bool want = h->tune.use_byte_table &&
+                      bytes <= (uint64_t)h->tune.byte_table_max_mb * (1ull << 20);
+    if (!want) {
+        if (h->d_tab) {
+            RAMBO_TRY(cudaStreamSynchronize(h->stream));
+            cudaDeviceSynchronize();
+            cudaFree(h->d_tab);
+            h->d_tab = nullptr;
+        }
+        return RAMBO_OK;
+    }
+    if (!h->d_tab) {
+        cudaDeviceSynchronize();
+        RAMBO_TRY(cudaMalloc(&h->d_tab, bytes));
+    }
+    RAMBO_TRY(launch_build_bytetab(h->d_docbits, g.B, g.R, g.W, h->d_tab, h->sm_count, h->stream));
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    return RAMBO_OK;
+}
+
 // Workspace layouts (offsets are 256-byte aligned).
 struct SeqWs {
     size_t kcum, bsum, acc, total;
@@ -145,7 +230,10 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     uint64_t *bsum = reinterpret_cast<uint64_t *>(w + L.bsum);
     uint32_t *acc = reinterpret_cast<uint32_t *>(w + L.acc);
     const Aligned al = align_packed(packed, packed_bytes);
-    RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+    {
+        StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
+        RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+    }
     RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
     ProbeArgs a{};
     a.index = h->d_index;
@@ -163,9 +251,16 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     a.n = n;
     a.acc = acc;
     a.err = h->d_err;
-    RAMBO_TRY(launch_probe_seqs(a, g, h->sm_count, s));
-    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out};
-    RAMBO_TRY(launch_expand(e, h->sm_count, s));
+    a.min_chunk = h->tune.probe_min_kmers_per_warp;
+    {
+        StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 1);
+        RAMBO_TRY(launch_probe_seqs(a, g, probe_grid(h), s));
+    }
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab};
+    {
+        StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
+        RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
+    }
     return RAMBO_OK;
 }
 
@@ -186,9 +281,16 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
     a.n = n;
     a.acc = acc;
     a.err = h->d_err;
-    RAMBO_TRY(launch_probe_kmers(a, g, h->sm_count, s));
-    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out};
-    RAMBO_TRY(launch_expand(e, h->sm_count, s));
+    a.min_chunk = h->tune.probe_min_kmers_per_warp;
+    {
+        StageScope sc(h, RAMBO_STAGE_PROBE_KMERS, s, 1);
+        RAMBO_TRY(launch_probe_kmers(a, g, probe_grid(h), s));
+    }
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab};
+    {
+        StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
+        RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
+    }
     return RAMBO_OK;
 }
 
@@ -200,8 +302,14 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     uint64_t *kcum = reinterpret_cast<uint64_t *>(w + L.kcum);
     uint64_t *bsum = reinterpret_cast<uint64_t *>(w + L.bsum);
     const Aligned al = align_packed(packed, packed_bytes);
-    RAMBO_TRY(launch_register_docs(doc_ids, n, h->d_phi, g.K, g.R, g.B, g.W, h->d_docbits, h->d_err, s));
-    RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+    {
+        StageScope sc(h, RAMBO_STAGE_REGISTER, s, 1);
+        RAMBO_TRY(launch_register_docs(doc_ids, n, h->d_phi, g.K, g.R, g.B, g.W, h->d_docbits, h->d_err, s));
+    }
+    {
+        StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
+        RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+    }
     InsertArgs a{};
     a.index = h->d_index;
     a.m = g.m;
@@ -222,7 +330,14 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     a.kcum = kcum;
     a.n = n;
     a.err = h->d_err;
-    RAMBO_TRY(launch_insert(a, h->sm_count, s));
+    {
+        StageScope sc(h, RAMBO_STAGE_INSERT, s, 1);
+        RAMBO_TRY(launch_insert(a, h->sm_count, s));
+    }
+    if (h->d_tab) {
+        StageScope sc(h, RAMBO_STAGE_REGISTER, s, 1);
+        RAMBO_TRY(launch_build_bytetab(h->d_docbits, g.B, g.R, g.W, h->d_tab, h->sm_count, s));
+    }
     return RAMBO_OK;
 }
 
@@ -330,6 +445,12 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     if ((rc = cuda_rc(cudaMemsetAsync(h->d_err, 0, 4, h->stream)))) return fail(rc);
     if ((rc = cuda_rc(launch_partition(h->d_phi, K, R, B, seed, h->stream)))) return fail(rc);
     if ((rc = cuda_rc(cudaStreamSynchronize(h->stream)))) return fail(rc);
+    h->tune.probe_ctas_per_sm = 0;
+    h->tune.probe_min_kmers_per_warp = 0;
+    h->tune.expand_ctas_per_sm = 8;
+    h->tune.use_byte_table = 1;
+    h->tune.byte_table_max_mb = 64;
+    if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
 }
@@ -343,6 +464,12 @@ int rambo_destroy(rambo_t *h) {
     cudaFree(h->d_phi);
     cudaFree(h->d_err);
     cudaFree(h->d_stage);
+    cudaFree(h->d_tab);
+    for (auto &p : h->pending) {
+        cudaEventDestroy(p.start);
+        cudaEventDestroy(p.stop);
+    }
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return RAMBO_OK;
@@ -527,6 +654,65 @@ int rambo_copy_partition(const rambo_t *h, uint32_t *dst) {
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
     RAMBO_TRY(cudaMemcpy(dst, h->d_phi, (uint64_t)h->g.K * h->g.R * 4, cudaMemcpyDeviceToHost));
+    return RAMBO_OK;
+}
+
+int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out) {
+    if (!h || !out) return RAMBO_EINVAL;
+    *out = h->tune;
+    return RAMBO_OK;
+}
+
+int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
+    if (!h || !t) return RAMBO_EINVAL;
+    if (t->probe_ctas_per_sm > 32 || t->expand_ctas_per_sm == 0 || t->expand_ctas_per_sm > 64 ||
+        t->probe_min_kmers_per_warp > (1u << 24))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    h->tune = *t;
+    return apply_bytetab(h);
+}
+
+int rambo_profile_reset(rambo_t *h, uint32_t stage_mask) {
+    if (!h) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    for (auto &p : h->pending) {
+        cudaEventSynchronize(p.stop);
+        h->event_pool.push_back(p.start);
+        h->event_pool.push_back(p.stop);
+    }
+    h->pending.clear();
+    h->prof_mask = stage_mask;
+    for (int i = 0; i < RAMBO_NUM_STAGES; ++i) {
+        h->launches[i] = 0;
+        h->timed[i] = 0;
+        h->ms[i] = 0.0;
+    }
+    return RAMBO_OK;
+}
+
+int rambo_profile_read(rambo_t *h, rambo_profile_t *out) {
+    if (!h || !out) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    for (auto &p : h->pending) {
+        RAMBO_TRY(cudaEventSynchronize(p.stop));
+        float ms = 0.f;
+        RAMBO_TRY(cudaEventElapsedTime(&ms, p.start, p.stop));
+        h->ms[p.stage] += ms;
+        h->timed[p.stage] += 1;
+        h->event_pool.push_back(p.start);
+        h->event_pool.push_back(p.stop);
+    }
+    h->pending.clear();
+    for (int i = 0; i < RAMBO_NUM_STAGES; ++i) {
+        out->launches[i] = h->launches[i];
+        out->timed[i] = h->timed[i];
+        out->ms[i] = h->ms[i];
+    }
     return RAMBO_OK;
 }
 

@@ -182,6 +182,7 @@ struct ProbeArgs {
     // output: per query Gw words (bucket-space AND over its k-mers)
     uint32_t *acc;
     uint32_t *err;
+    uint32_t min_chunk;      // minimum k-mers per warp (0 = default)
 };
 
 struct ExpandArgs {
@@ -190,6 +191,7 @@ struct ExpandArgs {
     uint32_t Gw, B, R, W;
     const uint32_t *docbits; // R*B*W
     uint32_t *out;           // n x W
+    const uint32_t *tab;     // byte table (R*ceil(B/8)*256*W) or null
 };
 
 struct InsertArgs {
@@ -223,5 +225,8 @@ cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_probe_seqs(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 cudaError_t launch_expand(const ExpandArgs &a, int sm_count, cudaStream_t s);
+uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W);
+cudaError_t launch_build_bytetab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
+                                 uint32_t *tab, int sm_count, cudaStream_t s);
 
 }  // namespace rgpu

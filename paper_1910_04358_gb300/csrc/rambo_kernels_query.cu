@@ -58,10 +58,11 @@ __device__ __forceinline__ void flush_slice(uint32_t *acc, uint64_t q, uint32_t 
 
 // Per-warp contiguous range of the flattened k-mer index space [0, T).
 template <int STEP>
-__device__ __forceinline__ void warp_range(uint64_t T, uint64_t &c0, uint64_t &c1) {
+__device__ __forceinline__ void warp_range(uint64_t T, uint32_t min_chunk, uint64_t &c0, uint64_t &c1) {
     const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     uint64_t per = (T + nwarps - 1) / nwarps;
+    if (per < min_chunk) per = min_chunk;
     per = (per + STEP - 1) / STEP * STEP;
     if (per < 2 * STEP) per = 2 * STEP;
     c0 = warp * per;
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_seqs(ProbeArgs a) {
 
     const uint64_t T = a.kcum[a.n];
     uint64_t c0, c1;
-    warp_range<STEP>(T, c0, c1);
+    warp_range<STEP>(T, a.min_chunk, c0, c1);
     if (c0 >= T) return;
     const uint64_t q_first = find_query(a.kcum, a.n, c0);
 
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_kmers(ProbeArgs a) {
 
     const uint64_t T = a.n;
     uint64_t c0, c1;
-    warp_range<STEP>(T, c0, c1);
+    warp_range<STEP>(T, a.min_chunk, c0, c1);
     if (c0 >= T) return;
     const uint64_t kbits = kmask(a.k);
 
@@ -259,56 +260,106 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_kmers(ProbeArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// expand: one CTA per query (grid-stride).  The passing buckets of each
-// repetition are listed in shared memory; output word w of the K-bit mask is
-// AND over r of (OR over listed b of DocBits[r][b][w]).  A repetition with no
-// passing bucket makes the answer empty.
-constexpr int EXPAND_THREADS = 128;
+// expand.  Work unit = (query, chunk of 32*C output words); one warp per unit
+// (grid-stride), no block barriers.  For repetition r the bucket row is bits
+// [r*B, r*B+B) of the query's bucket mask; the union of the passing buckets'
+// document bitmaps is built byte by byte: a zero byte costs nothing, a byte
+// with one set bit costs one DocBits row, a byte with several set bits costs
+// one row of the byte table (the precomputed OR of DocBits over that 8-bucket
+// pattern) when the table exists, else one row per set bit.  The answer is
+// the AND of the R unions; a repetition with no passing bucket, or an
+// all-zero running AND, ends the unit early.
+constexpr int EXPAND_THREADS = 256;
 
-template <bool USE_LIST>
+template <int C>
 __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(ExpandArgs a) {
-    extern __shared__ uint32_t smem[];
-    uint32_t *bm = smem;                // Gw words: the query's bucket mask
-    uint32_t *cnt = bm + a.Gw;          // R counters
-    uint32_t *lst = cnt + a.R;          // R*B bucket lists (USE_LIST)
-    const uint32_t RB = a.R * a.B;
-    for (uint64_t q = blockIdx.x; q < a.n; q += gridDim.x) {
-        for (uint32_t i = threadIdx.x; i < a.Gw; i += blockDim.x) bm[i] = a.acc[q * a.Gw + i];
-        for (uint32_t r = threadIdx.x; r < a.R; r += blockDim.x) cnt[r] = 0;
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < RB; i += blockDim.x) {
-            if ((bm[i >> 5] >> (i & 31)) & 1u) {
-                const uint32_t r = i / a.B;
-                const uint32_t slot = atomicAdd(&cnt[r], 1u);
-                if (USE_LIST) lst[r * a.B + slot] = i - r * a.B;
-            }
-        }
-        __syncthreads();
-        bool empty = false;
-        for (uint32_t r = 0; r < a.R; ++r) empty |= (cnt[r] == 0);
-        uint32_t *out = a.out + q * a.W;
-        for (uint32_t w = threadIdx.x; w < a.W; w += blockDim.x) {
-            uint32_t res = 0;
-            if (!empty) {
-                res = FULL;
-                for (uint32_t r = 0; r < a.R && res; ++r) {
-                    const uint32_t *db = a.docbits + (uint64_t)r * a.B * a.W + w;
-                    uint32_t o = 0;
-                    if (USE_LIST) {
-                        const uint32_t c = cnt[r];
-                        for (uint32_t i = 0; i < c; ++i) o |= __ldg(db + (uint64_t)lst[r * a.B + i] * a.W);
-                    } else {
-                        for (uint32_t b = 0; b < a.B; ++b) {
-                            const uint32_t i = r * a.B + b;
-                            if ((bm[i >> 5] >> (i & 31)) & 1u) o |= __ldg(db + (uint64_t)b * a.W);
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * (EXPAND_THREADS / 32) + threadIdx.x / 32;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (EXPAND_THREADS / 32);
+    const uint32_t chunks = (a.W + 32 * C - 1) / (32 * C);
+    const uint64_t units = a.n * chunks;
+    const uint32_t NJ = (a.B + 7) / 8;
+    for (uint64_t u = warp; u < units; u += nwarps) {
+        const uint64_t q = u / chunks;
+        const uint32_t w0 = (uint32_t)(u % chunks) * 32 * C + lane;
+        const uint32_t *bm = a.acc + q * a.Gw;
+        uint32_t res[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) res[c] = FULL;
+        bool dead = false;
+        for (uint32_t r = 0; r < a.R && !dead; ++r) {
+            uint32_t o[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) o[c] = 0;
+            bool any = false;
+            const uint32_t lo = r * a.B;
+            for (uint32_t j = 0; j < NJ; ++j) {
+                // byte j of the row: buckets 8j .. 8j+7 at bits lo+8j ..
+                const uint32_t bit = lo + 8 * j;
+                uint64_t two = __ldg(bm + (bit >> 5));
+                if ((bit & 31) > 24 && (bit >> 5) + 1 < a.Gw)
+                    two |= (uint64_t)__ldg(bm + (bit >> 5) + 1) << 32;
+                uint32_t v = (uint32_t)(two >> (bit & 31)) & 0xffu;
+                const uint32_t nb = a.B - 8 * j < 8 ? a.B - 8 * j : 8;
+                v &= (1u << nb) - 1u;
+                if (!v) continue;
+                any = true;
+                if (a.tab && (v & (v - 1))) {
+                    const uint32_t *row = a.tab + ((uint64_t)(r * NJ + j) * 256 + v) * a.W;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const uint32_t w = w0 + 32 * c;
+                        if (w < a.W) o[c] |= __ldg(row + w);
+                    }
+                } else {
+                    while (v) {
+                        const uint32_t b = 8 * j + __ffs(v) - 1;
+                        v &= v - 1;
+                        const uint32_t *row = a.docbits + (uint64_t)(lo + b) * a.W;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) {
+                            const uint32_t w = w0 + 32 * c;
+                            if (w < a.W) o[c] |= __ldg(row + w);
                         }
                     }
-                    res &= o;
                 }
             }
-            out[w] = res;
+            uint32_t nz = 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                res[c] &= o[c];
+                nz |= res[c];
+            }
+            if (!any || !__any_sync(FULL, nz)) dead = true;
         }
-        __syncthreads();
+        uint32_t *out = a.out + q * a.W;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const uint32_t w = w0 + 32 * c;
+            if (w < a.W) out[w] = dead ? 0u : res[c];
+        }
+    }
+}
+
+// Byte table: tab[((r*NJ + j)*256 + v)*W + w] = OR over set bits i of v
+// (8j+i < B) of DocBits[r][8j+i][w].
+__global__ void k_build_bytetab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
+                                uint32_t *tab) {
+    const uint32_t NJ = (B + 7) / 8;
+    const uint64_t total = (uint64_t)R * NJ * 256 * W;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)(i % W);
+        const uint64_t rest = i / W;
+        const uint32_t v = (uint32_t)(rest % 256);
+        const uint64_t rj = rest / 256;
+        const uint32_t j = (uint32_t)(rj % NJ), r = (uint32_t)(rj / NJ);
+        uint32_t o = 0;
+        for (uint32_t t = 0; t < 8; ++t) {
+            const uint32_t b = 8 * j + t;
+            if (((v >> t) & 1u) && b < B) o |= docbits[((uint64_t)r * B + b) * W + w];
+        }
+        tab[i] = o;
     }
 }
 
@@ -323,14 +374,15 @@ int blocks_per_sm(KernelT kernel, int threads, size_t smem) {
 template <int SW, int LPG, int ETA>
 cudaError_t launch_probe_t(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s,
                            bool kmers) {
+    // sm_count > 0: SMs x occupancy maximum; sm_count < 0: -sm_count CTAs
     dim3 grid, block(PROBE_THREADS);
     if (kmers) {
         static int occ = blocks_per_sm(k_probe_kmers<SW, LPG, ETA>, PROBE_THREADS, 0);
-        grid = dim3(sm_count * occ, g.chunks);
+        grid = dim3(sm_count > 0 ? sm_count * occ : -sm_count, g.chunks);
         k_probe_kmers<SW, LPG, ETA><<<grid, block, 0, s>>>(a);
     } else {
         static int occ = blocks_per_sm(k_probe_seqs<SW, LPG, ETA>, PROBE_THREADS, 0);
-        grid = dim3(sm_count * occ, g.chunks);
+        grid = dim3(sm_count > 0 ? sm_count * occ : -sm_count, g.chunks);
         k_probe_seqs<SW, LPG, ETA><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
@@ -372,23 +424,28 @@ cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_cou
 
 cudaError_t launch_expand(const ExpandArgs &a, int sm_count, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    const size_t list_smem = (size_t)(a.Gw + a.R + (size_t)a.R * a.B) * 4;
-    const size_t flat_smem = (size_t)(a.Gw + a.R) * 4;
-    const bool use_list = list_smem <= 96 * 1024;
-    const size_t smem = use_list ? list_smem : flat_smem;
-    if (smem > 48 * 1024) {
-        cudaError_t e = use_list ? cudaFuncSetAttribute(k_expand<true>,
-                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)smem)
-                                 : cudaFuncSetAttribute(k_expand<false>,
-                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)smem);
-        if (e != cudaSuccess) return e;
+    const uint32_t wc = (a.W + 31) / 32;
+    const int C = wc >= 8 ? 8 : wc >= 4 ? 4 : wc >= 2 ? 2 : 1;
+    const uint64_t units = a.n * ((a.W + 32 * C - 1) / (32 * C));
+    uint64_t blocks = (units + EXPAND_THREADS / 32 - 1) / (EXPAND_THREADS / 32);
+    const uint64_t cap = (uint64_t)sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    switch (C) {
+        case 1: k_expand<1><<<(unsigned)blocks, EXPAND_THREADS, 0, s>>>(a); break;
+        case 2: k_expand<2><<<(unsigned)blocks, EXPAND_THREADS, 0, s>>>(a); break;
+        case 4: k_expand<4><<<(unsigned)blocks, EXPAND_THREADS, 0, s>>>(a); break;
+        default: k_expand<8><<<(unsigned)blocks, EXPAND_THREADS, 0, s>>>(a); break;
     }
-    uint64_t blocks = (uint64_t)sm_count * 16;
-    if (blocks > a.n) blocks = a.n;
-    if (use_list) k_expand<true><<<(unsigned)blocks, EXPAND_THREADS, smem, s>>>(a);
-    else k_expand<false><<<(unsigned)blocks, EXPAND_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W) {
+    return (uint64_t)R * ((B + 7) / 8) * 256 * W;
+}
+
+cudaError_t launch_build_bytetab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
+                                 uint32_t *tab, int sm_count, cudaStream_t s) {
+    k_build_bytetab<<<sm_count * 8, 256, 0, s>>>(docbits, B, R, W, tab);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,12 @@ def load():
             "rambo_copy_index": (i, [p, u64, u64, p]),
             "rambo_copy_docbits": (i, [p, p]),
             "rambo_copy_partition": (i, [p, p]),
+            "rambo_profile_reset": (i, [p, u32]),
+            "rambo_profile_read": (i, [p, C.c_void_p]),
+            "rambo_get_tuning": (i, [p, C.c_void_p]),
+            "rambo_set_tuning": (i, [p, C.c_void_p]),
+            "rambo_probe_gather": (i, [p, u64, u32, u64, u32, u64, p, p]),
+            "rambo_set_l2_fetch_granularity": (i, [i, C.POINTER(i)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -135,6 +141,39 @@ class Workspace:
             self.ptr = (base + 255) // 256 * 256
             self.nbytes = want
         return self.ptr, self.nbytes
+
+
+STAGES = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
+TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_per_sm",
+                 "use_byte_table", "byte_table_max_mb")
+
+
+class _Tuning(C.Structure):
+    _fields_ = [(f, C.c_uint32) for f in TUNING_FIELDS]
+
+
+def probe_gather(buf, record_bytes: int, n_probes: int, variant: int = 0, seed: int = 1,
+                 sink=None, stream=None):
+    """Random-record gather over a torch uint8 CUDA tensor (measurement support)."""
+    import torch
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.int64, device=buf.device)
+    _check(load().rambo_probe_gather(buf.data_ptr(), buf.numel(), record_bytes, n_probes, variant,
+                                     seed, sink.data_ptr(), _stream_handle(stream)),
+           "rambo_probe_gather")
+    return sink
+
+
+def set_l2_fetch_granularity(nbytes: int) -> int:
+    """Sets this process's L2 fetch granularity limit; returns the previous value."""
+    prev = C.c_int(0)
+    _check(load().rambo_set_l2_fetch_granularity(nbytes, C.byref(prev)),
+           "rambo_set_l2_fetch_granularity")
+    return prev.value
+
+
+class _Profile(C.Structure):
+    _fields_ = [("launches", C.c_uint64 * 6), ("timed", C.c_uint64 * 6), ("ms", C.c_double * 6)]
 
 
 class Index:
@@ -257,6 +296,31 @@ class Index:
 
     def sync(self, stream=None):
         _check(load().rambo_sync(self._h, _stream_handle(stream)), "rambo_sync")
+
+    # ------------------------------------------------------------- tuning
+    def get_tuning(self) -> dict:
+        t = _Tuning()
+        _check(load().rambo_get_tuning(self._h, C.addressof(t)), "rambo_get_tuning")
+        return {f: getattr(t, f) for f in TUNING_FIELDS}
+
+    def set_tuning(self, **kw):
+        cur = self.get_tuning()
+        cur.update(kw)
+        t = _Tuning(**{f: int(cur[f]) for f in TUNING_FIELDS})
+        _check(load().rambo_set_tuning(self._h, C.addressof(t)), "rambo_set_tuning")
+
+    # ---------------------------------------------------------- profiling
+    def profile_reset(self, timed_stages=()):
+        mask = 0
+        for st in timed_stages:
+            mask |= 1 << STAGES.index(st)
+        _check(load().rambo_profile_reset(self._h, mask), "rambo_profile_reset")
+
+    def profile_read(self) -> dict:
+        pr = _Profile()
+        _check(load().rambo_profile_read(self._h, C.addressof(pr)), "rambo_profile_read")
+        return {st: {"launches": pr.launches[i], "timed": pr.timed[i], "ms": pr.ms[i]}
+                for i, st in enumerate(STAGES)}
 
     # ------------------------------------------------------ introspection
     def copy_index(self, offset: int = 0, nbytes: int | None = None) -> np.ndarray:

@@ -163,6 +163,34 @@ def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k):
     assert np.array_equal(idx.query_kmers(kmers), o.query_kmers(kmers))
 
 
+def test_tuning_knobs_do_not_change_results(rambo_lib):
+    p = synth.Params(K=300, B=40, R=4, m=1 << 13, eta=2, k=31, seed=4)
+    rng = np.random.default_rng(77)
+    corpus = synth.family_corpus(rng, p, n_seeds=20, doc_len=500, sub_rate=0.02)
+    q = synth.sample_queries(rng, corpus, rng.integers(25, 300, size=400), 0.6)
+    kmers = synth.sample_kmers(rng, corpus, 800, p.k, 0.5)
+    o = oracle_index(p, corpus)
+    want_s, want_k = o.query_seqs(q.packed, q.offsets), o.query_kmers(kmers)
+    idx = gpu_index(rambo_lib, p, corpus)
+    settings = [dict(use_byte_table=0), dict(use_byte_table=1, byte_table_max_mb=64),
+                dict(probe_ctas_per_sm=1, probe_min_kmers_per_warp=4096),
+                dict(probe_ctas_per_sm=7, probe_min_kmers_per_warp=0, expand_ctas_per_sm=1),
+                dict(expand_ctas_per_sm=64, use_byte_table=0)]
+    for st in settings:
+        idx.set_tuning(**st)
+        assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want_s), st
+        assert np.array_equal(idx.query_kmers(kmers), want_k), st
+    # the byte table follows later inserts
+    idx.set_tuning(use_byte_table=1)
+    extra = synth.family_corpus(np.random.default_rng(5), synth.Params(K=10, B=p.B, R=p.R, m=p.m, eta=2),
+                                n_seeds=2, doc_len=300, sub_rate=0.0)
+    ids = np.arange(290, 300, dtype=np.uint32)
+    idx.insert_batch(ids, extra.packed, extra.offsets)
+    o.insert_batch(ids, extra.packed, extra.offsets)
+    assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets),
+                          o.query_seqs(q.packed, q.offsets))
+
+
 # ---------------------------------------------------------------- edge cases
 
 def test_edge_cases(rambo_lib):
