@@ -166,6 +166,24 @@ int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t
                          const uint64_t *base_offsets, uint32_t *out, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* Sequence query that allocates nothing.  The paper has no counterpart: this
+ * exists for callers that cannot allocate device memory -- hosts that own
+ * every device byte and forbid library allocations, and latency-critical
+ * threads that must never reach cudaMalloc/cudaFree (which can block on or
+ * synchronise the device).  Same arguments, results and errors as
+ * rambo_query_seqs_dev, but the workspace is one static device array of
+ * RAMBO_STATIC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  A batch whose rambo_query_seqs_workspace(h, n) exceeds
+ * RAMBO_STATIC_SCRATCH_BYTES is rejected with RAMBO_EINVAL before anything is
+ * enqueued.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device); make that first call before any
+ * stream capture.  Every call on a device shares the one array, so calls
+ * whose work can overlap on the GPU (different streams, or handles on the
+ * same device) race: serialise them. */
+#define RAMBO_STATIC_SCRATCH_BYTES (8u << 20)
+int rambo_query_seqs_noalloc(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
+                             const uint64_t *base_offsets, uint32_t *out, void *stream);
+
 /* Waits for `stream` and returns the first device-side error latched since
  * the last rambo_sync (then clears it), or RAMBO_OK. */
 int rambo_sync(rambo_t *h, void *stream);

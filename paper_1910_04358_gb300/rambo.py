@@ -77,6 +77,7 @@ def load():
             "rambo_set_tuning": (i, [p, C.c_void_p]),
             "rambo_probe_gather": (i, [p, u64, u32, u64, u32, u64, p, p]),
             "rambo_set_l2_fetch_granularity": (i, [i, C.POINTER(i)]),
+            "rambo_query_seqs_noalloc": (i, [p, u64, p, u64, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
