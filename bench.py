@@ -213,6 +213,36 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 
 
 # ---------------------------------------------------------------------------
+# serving (continuous batching vs plain fixed batches, same trace)
+
+
+def serving_section(idx, corpus, n_req: int, fracs=(0.25, 0.5, 0.75, 0.9), seed: int = 4):
+    from paper_1910_04358_gb300 import serve, synth
+    rng = np.random.default_rng([synth.GEN_SEED_BASE + 4, seed])
+    _, lengths = synth.serving_trace(rng, n_req, rate_per_s=1.0)
+    # saturation: every request present at t = 0
+    reqs0 = serve.make_requests(corpus, np.zeros(n_req), lengths, rng)
+    eng = serve.ServingEngine(idx, slots=4, max_batch_queries=1024, max_batch_bytes=2 << 20,
+                              mask_budget_bytes=max(64 << 20, 4 * 1024 * idx.W * 4))
+    eng.serve(reqs0[: min(n_req, 500)])  # warm
+    sat = eng.serve(reqs0).summary()
+    sat_rps = n_req / sat["wall_s"]
+    out = {"requests_per_rate": n_req, "length_dist": "log-normal median 300 bp, sigma 1, [31, 10^4]",
+           "saturation": {"requests_per_s": sat_rps, "bp_per_s": sat["bp_per_s"],
+                          "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]},
+           "rates": []}
+    for f in fracs:
+        arrivals = np.cumsum(rng.exponential(1.0 / (f * sat_rps), size=n_req))
+        reqs = [serve.Request(r.rid, r.packed, r.n_bases, float(a)) for r, a in zip(reqs0, arrivals)]
+        cont = eng.serve(reqs).summary()
+        plain = serve.plain_batched(idx, reqs, batch_size=256).summary()
+        out["rates"].append({"offered_frac_of_saturation": f, "offered_requests_per_s": f * sat_rps,
+                             "continuous": {k: cont[k] for k in ("p50_ms", "p99_ms", "bp_per_s", "batches", "max_in_flight")},
+                             "plain_batch256": {k: plain[k] for k in ("p50_ms", "p99_ms", "bp_per_s", "batches")}})
+    return out
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle legs
 
 
@@ -313,6 +343,8 @@ def run_ours(args):
         return torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
 
     idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=local)
+    if args.query_path is not None:
+        idx.set_tuning(query_path=args.query_path)
     info = idx.info
     # ---- build (Algorithm 1), timed separately
     d_ids, d_cp, d_co = to_dev(corpus.doc_ids, np.int32), to_dev(corpus.packed, np.uint8), \
@@ -343,6 +375,15 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     idx.sync()
+    tuned = None
+    if not args.no_autotune and args.query_path is None:
+        from paper_1910_04358_gb300 import autotune
+        outs = lambda: [t for t in (out_k, out_s) if t is not None]
+        tuned = autotune.autotune(idx, step, outs, reps=3)
+        log(f"[autotune] best {tuned['best']} {tuned['ms']:.4f} ms/step")
+        for _ in range(3):
+            step()
+        idx.sync()
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -381,11 +422,15 @@ def run_ours(args):
     dom = "probe_seqs" if q.n else "probe_kmers"
     dom_ms = prof[dom]["ms"] / max(prof[dom]["timed"], 1)
     alg_bytes = probe_algorithmic_bytes(info, n_seq_kmers, q.n, q.n_bases)
+    fused = idx.get_tuning()["query_path"] == 1
+    if fused:  # the fused launch also writes the answer masks
+        alg_bytes += q.n * idx.W * 4
     peak, peak_src = measured_peak_gbs()
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
     traffic = measured_traffic(args.workload, dom)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": f"k_probe_seqs",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_fused_prep+k_fused" if fused else "k_probe_seqs",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "bytes_per_kmer": probe_bytes_per_kmer(info), "avg_launch_ms": dom_ms,
                 "peak_source": peak_src}
@@ -423,6 +468,14 @@ def run_ours(args):
         e2e = {"value": total_kmers * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e, "steps": e2e_steps}
 
+    # ---- serving: continuous batching on the same resident index
+    serving = None
+    if not args.no_serving and rank == 0:
+        try:
+            serving = serving_section(idx, corpus, args.serving_requests)
+        except Exception as ex:  # report, do not hide
+            serving = {"error": repr(ex)}
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -452,6 +505,8 @@ def run_ours(args):
         "build": {"seconds": build_s, "kmers": insert_kmers, "kmers_per_s": insert_kmers / build_s,
                   "insert_kernel_ms": prof_b["insert"]["ms"] or None},
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "spot_check_vs_host_api": ok,
+        "tuning": idx.get_tuning(), "serving": serving,
+        "autotune": ({"trials": len(tuned["trials"]), "best_ms": tuned["ms"]} if tuned else None),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -471,6 +526,11 @@ def main():
     ap.add_argument("--workload", choices=["medium", "large", "tiny"], default="medium")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=4000)
+    ap.add_argument("--query-path", type=int, default=None,
+                    help="0 = prefix/probe/expand launches, 1 = persistent fused launch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -184,6 +184,15 @@ int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t
 int rambo_query_seqs_noalloc(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
                              const uint64_t *base_offsets, uint32_t *out, void *stream);
 
+/* rambo_query_seqs_dev with items given as separate ranges: item i is bases
+ * [begins[i], ends[i]) of `packed` (n entries each, device memory), so items
+ * may be placed anywhere -- e.g. each at a byte boundary of a buffer that
+ * concatenates independently packed requests.  Same workspace size as
+ * rambo_query_seqs_workspace(h, n). */
+int rambo_query_ranges_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
+                           const uint64_t *begins, const uint64_t *ends, uint32_t *out,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
 /* Waits for `stream` and returns the first device-side error latched since
  * the last rambo_sync (then clears it), or RAMBO_OK. */
 int rambo_sync(rambo_t *h, void *stream);
@@ -213,6 +222,15 @@ typedef struct {
     uint32_t expand_ctas_per_sm;       /* expansion grid cap = SMs x this (1..64)    */
     uint32_t use_byte_table;           /* 1: expand through a per-8-bucket OR table  */
     uint32_t byte_table_max_mb;        /* ... only if it fits this many MiB          */
+    uint32_t query_path;               /* sequence queries: 0 = prefix scan + probe +  */
+                                       /* expand launches; 1 = persistent fused launch */
+                                       /* with length-bucketed work queues (groups up  */
+                                       /* to 512 B; otherwise path 0 is used)          */
+    uint32_t fused_tile_kmers;         /* path 1: k-mers per tile of a long query      */
+    uint32_t fused_short_max;          /* path 1: queries with at most this many       */
+                                       /* k-mers are probed and expanded by one warp   */
+    uint32_t smem_docbits;             /* 1: expansion stages the bucket->document     */
+                                       /* bitmaps in shared memory when they fit       */
 } rambo_tuning_t;
 
 int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out);
@@ -226,11 +244,12 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t);
 /* Random-record gather on the current device: n_probes reads of
  * record_bytes (16..512, power of two) at pseudo-random record indices of
  * `buf` (device, 16-byte aligned, buf_bytes long), with load instruction
- * variant 0..5 (0 = the probe kernels' streaming load).  XOR of the data goes
+ * variant 0..5 (0 = the probe kernels' streaming load) and `unroll` (4, 8, 16
+ * or 32) 16-byte loads in flight per lane.  XOR of the data goes
  * to the 8-byte device word `sink`.  Asynchronous on `stream`. */
 int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t record_bytes,
-                       uint64_t n_probes, uint32_t load_variant, uint64_t seed, void *sink,
-                       void *stream);
+                       uint64_t n_probes, uint32_t load_variant, uint32_t unroll, uint64_t seed,
+                       void *sink, void *stream);
 
 /* Reads (into *previous) and, if bytes > 0, sets the current context's L2
  * fetch granularity limit (32, 64 or 128 bytes).  A per-process context

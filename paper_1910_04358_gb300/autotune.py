@@ -1,0 +1,111 @@
+"""Autotuner for the query launch shapes.
+
+Picks, for one index and one representative batch, the query path (separate
+prefix/probe/expand launches or the persistent fused launch with
+length-bucketed queues), the probe grid (CTAs per SM), the minimum k-mers a
+warp takes, the fused path's tile size and short-query threshold, and the
+expansion grid and byte-table policy.  It times the batch under each
+candidate with CUDA events on the launching stream and insists that every
+candidate returns exactly the same answer bits as the first one (the knobs
+change launch shapes only).  Search is coordinate descent: one knob at a
+time, in the order of KNOBS, keeping the best value before moving on.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+KNOBS = (
+    ("query_path", (0, 1)),
+    ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
+    ("fused_tile_kmers", (256, 512, 1024, 2048, 4096)),
+    ("fused_short_max", (64, 256, 1024, 4096)),
+    ("probe_min_kmers_per_warp", (0, 256, 1024, 4096)),
+    ("expand_ctas_per_sm", (2, 4, 8, 16, 32)),
+    ("use_byte_table", (0, 1)),
+    ("smem_docbits", (0, 1)),
+)
+
+
+def _time(run, reps: int):
+    import torch
+    stream = torch.cuda.current_stream()
+    run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def autotune(idx, run, outputs, reps: int = 5, knobs=KNOBS, verbose: bool = False) -> dict:
+    """Tunes `idx` for the batch that `run()` enqueues on the current stream.
+
+    `outputs()` returns the tensors holding the batch's answers after a run;
+    every candidate's answers must equal the first candidate's bit for bit.
+    Leaves the best tuning set on `idx` and returns
+    {"best": tuning, "ms": best time, "trials": [...]}.
+    """
+    import torch
+    base = idx.get_tuning()
+    run()
+    idx.sync()
+    ref = [t.clone() for t in outputs()]
+    best_cfg, best_ms = dict(base), _time(run, reps)
+    trials = [{"tuning": dict(base), "ms": best_ms}]
+    for knob, values in knobs:
+        for v in values:
+            if best_cfg.get(knob) == v:
+                continue
+            cand = dict(best_cfg)
+            cand[knob] = v
+            if knob in ("fused_tile_kmers", "fused_short_max") and cand["query_path"] != 1:
+                continue
+            idx.set_tuning(**cand)
+            ms = _time(run, reps)
+            idx.sync()
+            got = outputs()
+            for a, b in zip(ref, got):
+                if not torch.equal(a, b):
+                    idx.set_tuning(**base)
+                    raise RuntimeError(f"tuning {cand} changed the answers")
+            trials.append({"tuning": cand, "ms": ms})
+            if verbose:
+                print(f"autotune {knob}={v}: {ms:.4f} ms (best {best_ms:.4f})", flush=True)
+            if ms < best_ms:
+                best_cfg, best_ms = cand, ms
+    idx.set_tuning(**best_cfg)
+    return {"best": best_cfg, "ms": best_ms, "trials": trials}
+
+
+def cache_key(idx, n_queries: int, n_kmers: int) -> str:
+    i = idx.info
+    return (f"K{i['K']}_B{i['B']}_R{i['R']}_m{i['m']}_eta{i['eta']}_k{i['k']}"
+            f"_n{n_queries}_kpq{n_kmers // max(n_queries, 1)}")
+
+
+def load_cached(path: str, key: str):
+    try:
+        with open(path) as f:
+            return json.load(f).get(key)
+    except Exception:
+        return None
+
+
+def store_cached(path: str, key: str, tuning: dict):
+    data = {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except Exception:
+        pass
+    data[key] = tuning
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)

@@ -173,14 +173,17 @@ int apply_bytetab(rambo_t *h) {
 
 // Workspace layouts (offsets are 256-byte aligned).
 struct SeqWs {
-    size_t kcum, bsum, acc, total;
+    size_t kcum, bsum, acc, qcnt, slist, done, total;
 };
 SeqWs seq_ws(const Geometry &g, uint64_t n) {
     SeqWs w;
     w.kcum = 0;
     w.bsum = align_up((n + 1) * 8);
     w.acc = w.bsum + align_up((kmer_prefix_block_sums(n) + 1) * 8);
-    w.total = w.acc + align_up(n * (uint64_t)g.Gw * 4);
+    w.qcnt = w.acc + align_up(n * (uint64_t)g.Gw * 4);
+    w.slist = w.qcnt + ALIGN;
+    w.done = w.slist + align_up(n * 4);
+    w.total = w.done + align_up(n * 4);
     return w;
 }
 
@@ -221,8 +224,10 @@ Aligned align_packed(const uint8_t *packed, uint64_t packed_bytes) {
     return Aligned{packed - mis, packed_bytes + mis, (uint64_t)mis * 4};
 }
 
+// Items are [begins[i], ends[i]); a CSR batch passes (offsets, offsets + 1).
 int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
-                       const uint64_t *offsets, uint32_t *out, void *ws, cudaStream_t s) {
+                       const uint64_t *offsets, const uint64_t *ends, uint32_t *out, void *ws,
+                       cudaStream_t s) {
     const Geometry &g = h->g;
     const SeqWs L = seq_ws(g, n);
     char *w = static_cast<char *>(ws);
@@ -230,9 +235,45 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     uint64_t *bsum = reinterpret_cast<uint64_t *>(w + L.bsum);
     uint32_t *acc = reinterpret_cast<uint32_t *>(w + L.acc);
     const Aligned al = align_packed(packed, packed_bytes);
+    if (h->tune.query_path == 1 && fused_supported(g)) {
+        // persistent fused query: length-bucketed queues, probe + expand in one launch
+        ProbeArgs a{};
+        a.index = h->d_index;
+        a.m = g.m;
+        a.m_pow2 = (g.m & (g.m - 1)) == 0;
+        a.Gw = g.Gw;
+        a.eta = g.eta;
+        a.k = g.k;
+        a.seed32 = (uint32_t)g.seed;
+        a.packed = al.p;
+        a.packed_bytes = al.bytes;
+        a.base_shift = al.base_shift;
+        a.offsets = offsets;
+        a.ends = ends;
+        a.n = n;
+        a.err = h->d_err;
+        ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits};
+        FusedQueues qs{};
+        qs.counters = reinterpret_cast<uint32_t *>(w + L.qcnt);
+        qs.short_list = reinterpret_cast<uint32_t *>(w + L.slist);
+        qs.tile_prefix = kcum;
+        qs.done = reinterpret_cast<uint32_t *>(w + L.done);
+        qs.tile = h->tune.fused_tile_kmers;
+        qs.short_max = h->tune.fused_short_max;
+        qs.user_bases = packed_bytes * 4;
+        {
+            StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
+            RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s,
+                                         qs.tile, qs.short_max));
+        }
+        StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 2);
+        const int go = h->tune.probe_ctas_per_sm ? (int)(h->sm_count * h->tune.probe_ctas_per_sm) : 0;
+        RAMBO_TRY(launch_fused(a, e, g, qs, go, h->sm_count, s));
+        return RAMBO_OK;
+    }
     {
         StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
-        RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+        RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
     }
     RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
     ProbeArgs a{};
@@ -247,6 +288,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     a.packed_bytes = al.bytes;
     a.base_shift = al.base_shift;
     a.offsets = offsets;
+    a.ends = ends;
     a.kcum = kcum;
     a.n = n;
     a.acc = acc;
@@ -256,7 +298,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 1);
         RAMBO_TRY(launch_probe_seqs(a, g, probe_grid(h), s));
     }
-    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab};
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits};
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
         RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
@@ -286,7 +328,7 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
         StageScope sc(h, RAMBO_STAGE_PROBE_KMERS, s, 1);
         RAMBO_TRY(launch_probe_kmers(a, g, probe_grid(h), s));
     }
-    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab};
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits};
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
         RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
@@ -308,7 +350,7 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     }
     {
         StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
-        RAMBO_TRY(launch_kmer_prefix(offsets, n, g.k, al.base_shift, packed_bytes, kcum, bsum, h->d_err, s));
+        RAMBO_TRY(launch_kmer_prefix(offsets, offsets + 1, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
     }
     InsertArgs a{};
     a.index = h->d_index;
@@ -351,6 +393,7 @@ int read_and_clear_err(rambo_t *h) {
         RAMBO_TRY(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
         RAMBO_TRY(cudaStreamSynchronize(h->stream));
     }
+    if (e & ERR_QUEUE) return RAMBO_ETIMEOUT;
     if (e & ERR_DOC_RANGE) return RAMBO_ERANGE;
     if (e & (ERR_KMER_CODE | ERR_OFFSETS)) return RAMBO_EINVAL;
     return RAMBO_OK;
@@ -450,6 +493,10 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.expand_ctas_per_sm = 8;
     h->tune.use_byte_table = 1;
     h->tune.byte_table_max_mb = 64;
+    h->tune.query_path = 0;
+    h->tune.smem_docbits = 1;
+    h->tune.fused_tile_kmers = 1024;
+    h->tune.fused_short_max = 1024;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -539,7 +586,21 @@ int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
-    return query_seqs_enqueue(h, n, packed, packed_bytes, base_offsets, out, workspace,
+    return query_seqs_enqueue(h, n, packed, packed_bytes, base_offsets, base_offsets + 1, out,
+                              workspace, static_cast<cudaStream_t>(stream));
+}
+
+int rambo_query_ranges_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
+                           const uint64_t *begins, const uint64_t *ends, uint32_t *out,
+                           void *workspace, size_t workspace_bytes, void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n == 0) return RAMBO_OK;
+    if (n >= 0xffffffffULL || !begins || !ends || !out || !workspace || (!packed && packed_bytes) ||
+        workspace_bytes < seq_ws(h->g, n).total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    return query_seqs_enqueue(h, n, packed, packed_bytes, begins, ends, out, workspace,
                               static_cast<cudaStream_t>(stream));
 }
 
@@ -617,8 +678,8 @@ int rambo_query_seqs(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64
     int rc = stage_batch(h, n, packed, base_offsets, out_sz + seq_ws(h->g, n).total, &st);
     if (rc) return rc;
     uint32_t *d_out = reinterpret_cast<uint32_t *>(st.rest);
-    rc = query_seqs_enqueue(h, n, st.packed, st.packed_bytes + 16, st.offsets, d_out,
-                            st.rest + out_sz, h->stream);
+    rc = query_seqs_enqueue(h, n, st.packed, st.packed_bytes + 16, st.offsets, st.offsets + 1,
+                            d_out, st.rest + out_sz, h->stream);
     if (rc) return rc;
     RAMBO_TRY(cudaMemcpyAsync(out, d_out, n * (uint64_t)h->g.W * 4, cudaMemcpyDeviceToHost, h->stream));
     RAMBO_TRY(cudaStreamSynchronize(h->stream));
@@ -666,7 +727,8 @@ int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out) {
 int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
     if (!h || !t) return RAMBO_EINVAL;
     if (t->probe_ctas_per_sm > 32 || t->expand_ctas_per_sm == 0 || t->expand_ctas_per_sm > 64 ||
-        t->probe_min_kmers_per_warp > (1u << 24))
+        t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 1 || t->fused_tile_kmers == 0 ||
+        t->fused_tile_kmers > (1u << 24) || t->fused_short_max > (1u << 24) || t->smem_docbits > 1)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

@@ -40,14 +40,13 @@ __device__ __forceinline__ uint4 ld16(const uint4 *p) {
     return v;
 }
 
-// LPR lanes read one record of 16*LPR bytes; 8 independent records per lane
-// are in flight per iteration.
-template <int LPR, int V>
+// LPR lanes read one record of 16*LPR bytes; U independent 16-byte loads per
+// lane are in flight per iteration.
+template <int LPR, int V, int U>
 __global__ void __launch_bounds__(GATHER_THREADS) k_gather(const uint4 *buf, uint64_t n_records,
                                                            uint64_t n_probes, uint64_t seed,
                                                            unsigned long long *sink) {
     constexpr int RPW = 32 / LPR;  // records per warp instruction
-    constexpr int U = 8;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (uint64_t)blockIdx.x * (GATHER_THREADS / 32) + threadIdx.x / 32;
     const uint64_t nwarps = (uint64_t)gridDim.x * (GATHER_THREADS / 32);
@@ -70,27 +69,37 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(const uint4 *buf, uin
     if (x == 0x9e3779b97f4a7c15ULL) atomicXor(sink, x);  // practically never taken
 }
 
-template <int LPR>
+template <int LPR, int U>
 cudaError_t launch_gather_v(const void *buf, uint64_t n_records, uint64_t n_probes, uint32_t variant,
                             uint64_t seed, unsigned long long *sink, int blocks, cudaStream_t s) {
     const uint4 *b = static_cast<const uint4 *>(buf);
     switch (variant) {
-        case 0: k_gather<LPR, 0><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
-        case 1: k_gather<LPR, 1><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
-        case 2: k_gather<LPR, 2><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
-        case 3: k_gather<LPR, 3><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
-        case 4: k_gather<LPR, 4><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
-        default: k_gather<LPR, 5><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
+        case 0: k_gather<LPR, 0, U><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
+        case 1: k_gather<LPR, 1, U><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
+        case 2: k_gather<LPR, 2, U><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
+        case 3: k_gather<LPR, 3, U><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
+        case 4: k_gather<LPR, 4, U><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
+        default: k_gather<LPR, 5, U><<<blocks, GATHER_THREADS, 0, s>>>(b, n_records, n_probes, seed, sink); break;
     }
     return cudaGetLastError();
+}
+
+template <int LPR>
+cudaError_t launch_gather_u(const void *buf, uint64_t n_records, uint64_t n_probes, uint32_t variant,
+                            uint32_t unroll, uint64_t seed, unsigned long long *sink, int blocks,
+                            cudaStream_t s) {
+    if (unroll >= 32) return launch_gather_v<LPR, 32>(buf, n_records, n_probes, variant, seed, sink, blocks, s);
+    if (unroll >= 16) return launch_gather_v<LPR, 16>(buf, n_records, n_probes, variant, seed, sink, blocks, s);
+    if (unroll >= 8) return launch_gather_v<LPR, 8>(buf, n_records, n_probes, variant, seed, sink, blocks, s);
+    return launch_gather_v<LPR, 4>(buf, n_records, n_probes, variant, seed, sink, blocks, s);
 }
 
 }  // namespace
 }  // namespace rgpu
 
 extern "C" int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t record_bytes,
-                                  uint64_t n_probes, uint32_t load_variant, uint64_t seed,
-                                  void *sink, void *stream) {
+                                  uint64_t n_probes, uint32_t load_variant, uint32_t unroll,
+                                  uint64_t seed, void *sink, void *stream) {
     using namespace rgpu;
     if (!buf || !sink || load_variant > 5) return RAMBO_EINVAL;
     if (record_bytes != 16 && record_bytes != 32 && record_bytes != 64 && record_bytes != 128 &&
@@ -107,12 +116,12 @@ extern "C" int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t 
     auto *sk = static_cast<unsigned long long *>(sink);
     cudaError_t e;
     switch (record_bytes) {
-        case 16: e = launch_gather_v<1>(buf, n_records, n_probes, load_variant, seed, sk, blocks, s); break;
-        case 32: e = launch_gather_v<2>(buf, n_records, n_probes, load_variant, seed, sk, blocks, s); break;
-        case 64: e = launch_gather_v<4>(buf, n_records, n_probes, load_variant, seed, sk, blocks, s); break;
-        case 128: e = launch_gather_v<8>(buf, n_records, n_probes, load_variant, seed, sk, blocks, s); break;
-        case 256: e = launch_gather_v<16>(buf, n_records, n_probes, load_variant, seed, sk, blocks, s); break;
-        default: e = launch_gather_v<32>(buf, n_records, n_probes, load_variant, seed, sk, blocks, s); break;
+        case 16: e = launch_gather_u<1>(buf, n_records, n_probes, load_variant, unroll, seed, sk, blocks, s); break;
+        case 32: e = launch_gather_u<2>(buf, n_records, n_probes, load_variant, unroll, seed, sk, blocks, s); break;
+        case 64: e = launch_gather_u<4>(buf, n_records, n_probes, load_variant, unroll, seed, sk, blocks, s); break;
+        case 128: e = launch_gather_u<8>(buf, n_records, n_probes, load_variant, unroll, seed, sk, blocks, s); break;
+        case 256: e = launch_gather_u<16>(buf, n_records, n_probes, load_variant, unroll, seed, sk, blocks, s); break;
+        default: e = launch_gather_u<32>(buf, n_records, n_probes, load_variant, unroll, seed, sk, blocks, s); break;
     }
     return e == cudaSuccess ? RAMBO_OK : RAMBO_ECUDA;
 }

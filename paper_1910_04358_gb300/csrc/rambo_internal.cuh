@@ -14,6 +14,7 @@ enum : uint32_t {
     ERR_DOC_RANGE = 1u,     // document id >= K
     ERR_KMER_CODE = 2u,     // k-mer code with a bit at or above 2k
     ERR_OFFSETS = 4u,       // decreasing offsets or offsets past the buffer
+    ERR_QUEUE = 8u,         // a work-queue claim loop exceeded its bound
 };
 
 // ---------------------------------------------------------------------------
@@ -174,7 +175,8 @@ struct ProbeArgs {
     const uint8_t *packed;   // 8-byte aligned base of the packed stream
     uint64_t packed_bytes;   // readable bytes from `packed`
     uint64_t base_shift;     // bases to add to every offset (alignment fix-up)
-    const uint64_t *offsets; // n+1
+    const uint64_t *offsets; // n item begins (base index)
+    const uint64_t *ends;    // n item ends (CSR batches: offsets + 1)
     const uint64_t *kcum;    // n+1 exclusive prefix of k-mer counts
     uint64_t n;
     // single k-mers
@@ -192,6 +194,7 @@ struct ExpandArgs {
     const uint32_t *docbits; // R*B*W
     uint32_t *out;           // n x W
     const uint32_t *tab;     // byte table (R*ceil(B/8)*256*W) or null
+    uint32_t smem_docbits;   // 1: stage DocBits in shared memory when it fits
 };
 
 struct InsertArgs {
@@ -214,9 +217,13 @@ struct InsertArgs {
 // status.
 cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, uint64_t seed,
                              cudaStream_t s);
-cudaError_t launch_kmer_prefix(const uint64_t *offsets, uint64_t n, uint32_t k, uint64_t base_shift,
+// Exclusive prefix (n+1 values) of the k-mer counts of items
+// [begins[i], ends[i]); with tile > 0, of the tile counts of the items with
+// more than short_max k-mers (ceil(k-mers / tile); shorter items count 0).
+cudaError_t launch_kmer_prefix(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
                                uint64_t packed_bytes, uint64_t *kcum, uint64_t *block_sums,
-                               uint32_t *err, cudaStream_t s);
+                               uint32_t *err, cudaStream_t s, uint32_t tile = 0,
+                               uint32_t short_max = 0);
 size_t kmer_prefix_block_sums(uint64_t n);
 cudaError_t launch_register_docs(const uint32_t *doc_ids, uint64_t n, const uint32_t *phi,
                                  uint32_t K, uint32_t R, uint32_t B, uint32_t W, uint32_t *docbits,
@@ -224,7 +231,23 @@ cudaError_t launch_register_docs(const uint32_t *doc_ids, uint64_t n, const uint
 cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_probe_seqs(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
-cudaError_t launch_expand(const ExpandArgs &a, int sm_count, cudaStream_t s);
+// Work queues of the persistent fused query (workspace arrays).
+struct FusedQueues {
+    uint32_t *counters;      // 4 words, zeroed by the launcher
+    uint32_t *short_list;    // n
+    const uint64_t *tile_prefix;  // n+1: exclusive prefix of long-query tile counts
+    uint32_t *done;          // n
+    uint32_t tile;           // k-mers per long tile
+    uint32_t short_max;      // longest short query (k-mers)
+    uint64_t user_bases;     // bases addressable from the caller's packed pointer
+};
+bool fused_supported(const Geometry &g);
+// p.acc is unused (the bucket masks of long queries are e.acc).
+cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry &g,
+                         const FusedQueues &qs, int grid_override, int sm_count, cudaStream_t s);
+
+// max_blocks caps the expansion grid
+cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, cudaStream_t s);
 uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W);
 cudaError_t launch_build_bytetab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
                                  uint32_t *tab, int sm_count, cudaStream_t s);

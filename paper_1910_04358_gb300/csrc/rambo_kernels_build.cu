@@ -31,15 +31,25 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr uint64_t SCAN_TILE = (uint64_t)SCAN_THREADS * SCAN_ITEMS;
 
-__device__ __forceinline__ uint64_t kmer_count(const uint64_t *offs, uint64_t i, uint32_t k,
-                                               uint64_t limit, uint32_t *err) {
-    const uint64_t b0 = offs[i], b1 = offs[i + 1];
+// Count of item i: its k-mers, or (tile > 0) the tiles of `tile` k-mers of
+// an item with more than short_max k-mers (0 for shorter items).
+struct CountMode {
+    uint32_t tile;
+    uint32_t short_max;
+};
+
+__device__ __forceinline__ uint64_t kmer_count(const uint64_t *begins, const uint64_t *ends,
+                                               uint64_t i, uint32_t k, uint64_t limit,
+                                               uint32_t *err, CountMode cm) {
+    const uint64_t b0 = begins[i], b1 = ends[i];
     if (b1 < b0 || b1 > limit) {
         if (err) atomicOr(err, ERR_OFFSETS);
         return 0;
     }
     const uint64_t L = b1 - b0;
-    return L >= k ? L - k + 1 : 0;
+    const uint64_t nk = L >= k ? L - k + 1 : 0;
+    if (cm.tile == 0) return nk;
+    return nk > cm.short_max ? (nk + cm.tile - 1) / cm.tile : 0;
 }
 
 // Block-wide exclusive scan of one value per thread; returns the prefix and
@@ -72,14 +82,14 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *t
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS)
-k_prefix_partial(const uint64_t *offs, uint64_t n, uint32_t k, uint64_t limit, uint64_t *bsum,
-                 uint32_t *err) {
+k_prefix_partial(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
+                 uint64_t limit, uint64_t *bsum, uint32_t *err, CountMode cm) {
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     uint64_t s = 0;
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         const uint64_t i = base + (uint64_t)j * SCAN_THREADS + threadIdx.x;
-        if (i < n) s += kmer_count(offs, i, k, limit, err);
+        if (i < n) s += kmer_count(begins, ends, i, k, limit, err, cm);
     }
     uint64_t total;
     block_exclusive_scan(s, &total);
@@ -102,13 +112,13 @@ k_prefix_blocks(uint64_t *bsum, uint64_t nblk, uint64_t *kcum, uint64_t n) {
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS)
-k_prefix_final(const uint64_t *offs, uint64_t n, uint32_t k, uint64_t limit, const uint64_t *bsum,
-               uint64_t *kcum) {
+k_prefix_final(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k, uint64_t limit,
+               const uint64_t *bsum, uint64_t *kcum, CountMode cm) {
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     uint64_t carry = bsum[blockIdx.x];
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         const uint64_t i = base + (uint64_t)j * SCAN_THREADS + threadIdx.x;
-        const uint64_t c = i < n ? kmer_count(offs, i, k, limit, nullptr) : 0;
+        const uint64_t c = i < n ? kmer_count(begins, ends, i, k, limit, nullptr, cm) : 0;
         uint64_t total;
         const uint64_t ex = block_exclusive_scan(c, &total);
         if (i < n) kcum[i] = carry + ex;
@@ -223,16 +233,16 @@ cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, 
 
 size_t kmer_prefix_block_sums(uint64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
-cudaError_t launch_kmer_prefix(const uint64_t *offsets, uint64_t n, uint32_t k, uint64_t base_shift,
+cudaError_t launch_kmer_prefix(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
                                uint64_t packed_bytes, uint64_t *kcum, uint64_t *block_sums,
-                               uint32_t *err, cudaStream_t s) {
-    (void)base_shift;
+                               uint32_t *err, cudaStream_t s, uint32_t tile, uint32_t short_max) {
     const uint64_t limit = packed_bytes * 4;  // bases addressable from the caller's pointer
     const uint64_t nblk = kmer_prefix_block_sums(n);
     if (nblk == 0) return cudaSuccess;
-    k_prefix_partial<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(offsets, n, k, limit, block_sums, err);
+    const CountMode cm{tile, short_max};
+    k_prefix_partial<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(begins, ends, n, k, limit, block_sums, err, cm);
     k_prefix_blocks<<<1, SCAN_THREADS, 0, s>>>(block_sums, nblk, kcum, n);
-    k_prefix_final<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(offsets, n, k, limit, block_sums, kcum);
+    k_prefix_final<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(begins, ends, n, k, limit, block_sums, kcum, cm);
     return cudaGetLastError();
 }
 

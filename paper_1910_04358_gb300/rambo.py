@@ -75,9 +75,10 @@ def load():
             "rambo_profile_read": (i, [p, C.c_void_p]),
             "rambo_get_tuning": (i, [p, C.c_void_p]),
             "rambo_set_tuning": (i, [p, C.c_void_p]),
-            "rambo_probe_gather": (i, [p, u64, u32, u64, u32, u64, p, p]),
+            "rambo_probe_gather": (i, [p, u64, u32, u64, u32, u32, u64, p, p]),
             "rambo_set_l2_fetch_granularity": (i, [i, C.POINTER(i)]),
             "rambo_query_seqs_noalloc": (i, [p, u64, p, u64, p, p, p]),
+            "rambo_query_ranges_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -146,7 +147,8 @@ class Workspace:
 
 STAGES = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
 TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_per_sm",
-                 "use_byte_table", "byte_table_max_mb")
+                 "use_byte_table", "byte_table_max_mb", "query_path", "fused_tile_kmers",
+                 "fused_short_max", "smem_docbits")
 
 
 class _Tuning(C.Structure):
@@ -154,13 +156,13 @@ class _Tuning(C.Structure):
 
 
 def probe_gather(buf, record_bytes: int, n_probes: int, variant: int = 0, seed: int = 1,
-                 sink=None, stream=None):
+                 sink=None, stream=None, unroll: int = 8):
     """Random-record gather over a torch uint8 CUDA tensor (measurement support)."""
     import torch
     if sink is None:
         sink = torch.zeros(1, dtype=torch.int64, device=buf.device)
     _check(load().rambo_probe_gather(buf.data_ptr(), buf.numel(), record_bytes, n_probes, variant,
-                                     seed, sink.data_ptr(), _stream_handle(stream)),
+                                     unroll, seed, sink.data_ptr(), _stream_handle(stream)),
            "rambo_probe_gather")
     return sink
 
@@ -293,6 +295,20 @@ class Index:
         _check(load().rambo_query_seqs_dev(self._h, max(n, 0), _t_ptr(packed), packed.numel(),
                                            _t_ptr(offsets), _t_ptr(out), wp, wn, s),
                "rambo_query_seqs_dev")
+        return out
+
+    def query_ranges_dev(self, packed, begins, ends, out=None, stream=None, workspace=None):
+        """Items [begins[i], ends[i]) of a packed uint8 CUDA tensor (int64 tensors)."""
+        import torch
+        n = begins.numel()
+        if out is None:
+            out = torch.empty((n, self.W), dtype=torch.int32, device=begins.device)
+        need = self.workspace_bytes("seqs", n)
+        s = _stream_handle(stream)
+        wp, wn = workspace if workspace is not None else self._workspace(s, need)
+        _check(load().rambo_query_ranges_dev(self._h, n, _t_ptr(packed), packed.numel(),
+                                             _t_ptr(begins), _t_ptr(ends), _t_ptr(out), wp, wn, s),
+               "rambo_query_ranges_dev")
         return out
 
     def sync(self, stream=None):

@@ -308,3 +308,71 @@ def serving_trace(rng, n: int, rate_per_s: float, median: float = 300.0, sigma: 
     arrivals = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
     lengths = np.clip(np.round(rng.lognormal(np.log(median), sigma, size=n)), lo, hi).astype(np.int64)
     return arrivals, lengths
+
+
+class StreamWorkload:
+    """Documents arriving in epochs, each followed by a query batch.
+
+    n_seeds uniform seed genomes of doc_len bases; every document is a copy of
+    a random seed with i.i.d. substitutions at `divergence`.  After epoch e the
+    query batch draws 70% of its sequences from documents inserted so far
+    (with 0.1% read errors) and 30% uniform, lengths U[qmin, qmax].
+    """
+
+    def __init__(self, params: Params, n_seeds: int, doc_len: int, divergence: float,
+                 epoch_docs: int, queries_per_epoch: int, qmin: int = 31, qmax: int = 2000,
+                 seed_salt: int = 0):
+        self.params = params
+        self.doc_len = doc_len
+        self.divergence = divergence
+        self.epoch_docs = epoch_docs
+        self.queries_per_epoch = queries_per_epoch
+        self.qmin, self.qmax = qmin, qmax
+        self.rng = np.random.default_rng([GEN_SEED_BASE + WORKLOAD_INDEX[STREAM], seed_salt])
+        self.seeds = [uniform_genome(self.rng, doc_len) for _ in range(n_seeds)]
+        self.n_epochs = (params.K + epoch_docs - 1) // epoch_docs
+        self.inserted = 0
+        self._docs_so_far: list[np.ndarray] = []
+
+    def epoch(self, e: int):
+        """(doc_ids, packed, offsets) of epoch e, then its query batch."""
+        lo = e * self.epoch_docs
+        hi = min(self.params.K, lo + self.epoch_docs)
+        s = PackedStream()
+        docs = []
+        for _ in range(lo, hi):
+            d = substitute(self.rng, self.seeds[int(self.rng.integers(0, len(self.seeds)))],
+                           self.divergence)
+            s.append(d)
+            docs.append(d)
+        packed, offs = s.finish()
+        self._docs_so_far.extend(docs)
+        self.inserted = hi
+        ids = np.arange(lo, hi, dtype=np.uint32)
+        # queries over everything inserted so far
+        n = self.queries_per_epoch
+        lengths = self.rng.integers(self.qmin, self.qmax + 1, size=n)
+        qs = PackedStream()
+        src = np.full(n, -1, dtype=np.int64)
+        for i in range(n):
+            L = int(lengths[i])
+            if self.rng.random() < 0.7:
+                d = int(self.rng.integers(0, hi))
+                doc = self._docs_so_far[d]
+                off = int(self.rng.integers(0, doc.size - L + 1))
+                qs.append(substitute(self.rng, doc[off:off + L], 0.001))
+                src[i] = d
+            else:
+                qs.append(uniform_genome(self.rng, L))
+        qp, qo = qs.finish()
+        return (ids, packed, offs), QueryBatch(qp, qo, src)
+
+
+def stream_workload(n_docs: int | None = None, doc_len: int = 50_000, n_seeds: int = 2000,
+                    epoch_docs: int = 1000, queries_per_epoch: int = 10_000,
+                    m: int | None = None) -> StreamWorkload:
+    """100,000 x 50 kbp documents from 2,000 seeds at 1% divergence, inserted
+    in epochs of 1,000; after each epoch 10^4 queries of 31..2,000 bp."""
+    p = WORKLOAD_PARAMS[STREAM]
+    p = Params(K=n_docs or p.K, B=p.B, R=p.R, m=m or p.m, eta=p.eta)
+    return StreamWorkload(p, n_seeds, doc_len, 0.01, epoch_docs, queries_per_epoch)

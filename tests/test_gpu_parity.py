@@ -147,14 +147,17 @@ SWEEP = [
 ]
 
 
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("K,B,R,m,eta,k", SWEEP)
-def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k):
+def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k, path):
     p = synth.Params(K=K, B=B, R=R, m=m, eta=eta, k=k, seed=K + B)
     rng = np.random.default_rng(K * 7 + B)
     corpus = synth.family_corpus(rng, p, n_seeds=max(1, K // 8), doc_len=400, sub_rate=0.02)
     q = synth.sample_queries(rng, corpus, rng.integers(max(1, k - 3), 200, size=300), 0.6)
     o = oracle_index(p, corpus)
     idx = gpu_index(rambo_lib, p, corpus, chunks=3)
+    # path 1 (persistent fused launch) with small tiles so long queries span tiles
+    idx.set_tuning(query_path=path, fused_tile_kmers=64, fused_short_max=40)
     assert_index_equal(idx, o, p)
     assert_docbits_equal(idx, o, p)
     assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets),
@@ -175,7 +178,15 @@ def test_tuning_knobs_do_not_change_results(rambo_lib):
     settings = [dict(use_byte_table=0), dict(use_byte_table=1, byte_table_max_mb=64),
                 dict(probe_ctas_per_sm=1, probe_min_kmers_per_warp=4096),
                 dict(probe_ctas_per_sm=7, probe_min_kmers_per_warp=0, expand_ctas_per_sm=1),
-                dict(expand_ctas_per_sm=64, use_byte_table=0)]
+                dict(expand_ctas_per_sm=64, use_byte_table=0),
+                dict(query_path=1, fused_tile_kmers=1024, fused_short_max=1024),
+                dict(query_path=1, fused_tile_kmers=32, fused_short_max=0),
+                dict(query_path=1, fused_tile_kmers=100, fused_short_max=1 << 20),
+                dict(query_path=1, fused_tile_kmers=64, fused_short_max=50, use_byte_table=1,
+                     probe_ctas_per_sm=1),
+                dict(query_path=0, smem_docbits=0),
+                dict(query_path=0, smem_docbits=1, expand_ctas_per_sm=1),
+                dict(query_path=1, smem_docbits=0, use_byte_table=0)]
     for st in settings:
         idx.set_tuning(**st)
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want_s), st
