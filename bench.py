@@ -376,11 +376,20 @@ def run_ours(args):
         step()
     idx.sync()
     tuned = None
+    tuning_source = "default"
     if not args.no_autotune and args.query_path is None:
         from paper_1910_04358_gb300 import autotune
-        outs = lambda: [t for t in (out_k, out_s) if t is not None]
-        tuned = autotune.autotune(idx, step, outs, reps=3)
-        log(f"[autotune] best {tuned['best']} {tuned['ms']:.4f} ms/step")
+        key = autotune.cache_key(idx, q.n + int(kmers.size), total_kmers)
+        cached = None if args.retune else autotune.load_cached(autotune.CACHE_FILE, key)
+        if cached:
+            idx.set_tuning(**cached)
+            tuning_source = f"cached ({os.path.relpath(autotune.CACHE_FILE, ROOT)})"
+        else:
+            outs = lambda: [t for t in (out_k, out_s) if t is not None]
+            tuned = autotune.autotune(idx, step, outs, reps=3)
+            log(f"[autotune] best {tuned['best']} {tuned['ms']:.4f} ms/step")
+            autotune.store_cached(autotune.CACHE_FILE, key, tuned["best"])
+            tuning_source = "autotuned in this run"
         for _ in range(3):
             step()
         idx.sync()
@@ -408,6 +417,39 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     prof = idx.profile_read()
     launches = sum(v["launches"] for v in prof.values())
+    ms_step_eager = ms_step
+
+    # ---- the same steps replayed from a captured CUDA graph (launch overhead gone)
+    graph = None
+    if not args.no_graph:
+        try:
+            idx.profile_reset()  # counting only: no event records inside the capture
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step()
+            per_step_launches = sum(v["launches"] for v in idx.profile_read().values())
+            g.replay()
+            torch.cuda.synchronize()
+            barrier(world)
+            torch.cuda.synchronize()
+            gs = torch.cuda.current_stream()
+            ev0.record(gs)
+            for _ in range(args.steps):
+                g.replay()
+            ev1.record(gs)
+            torch.cuda.synchronize()
+            barrier(world)
+            ms_g = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+            graph = {"ms_per_step": ms_g, "launches_per_step": per_step_launches}
+            if ms_g < ms_step:
+                ms_step = ms_g
+                launches = per_step_launches * args.steps
+            # the graph's answers are the eager answers
+            ok_graph = torch.equal(out_s, idx.query_seqs_dev(d_qp, d_qo))
+            idx.sync()
+            graph["answers_match_eager"] = bool(ok_graph)
+        except Exception as ex:
+            graph = {"error": repr(ex)}
     # per-stage breakdown from a separate profiled pass (every stage bracketed)
     idx.profile_reset(timed_stages=STAGES_ALL)
     for _ in range(min(args.steps, 20)):
@@ -417,6 +459,7 @@ def run_ours(args):
 
     value = total_kmers * world / (ms_step / 1e3)
     bp_s = bp * world / (ms_step / 1e3)
+    launch_mode = "cuda graph replay" if graph and graph.get("ms_per_step") == ms_step else "eager"
 
     # ---- roofline of the dominant kernel (sequence probe)
     dom = "probe_seqs" if q.n else "probe_kmers"
@@ -505,7 +548,8 @@ def run_ours(args):
         "build": {"seconds": build_s, "kmers": insert_kmers, "kmers_per_s": insert_kmers / build_s,
                   "insert_kernel_ms": prof_b["insert"]["ms"] or None},
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "spot_check_vs_host_api": ok,
-        "tuning": idx.get_tuning(), "serving": serving,
+        "launch_mode": launch_mode, "eager_ms_per_step": ms_step_eager, "graph": graph,
+        "tuning": idx.get_tuning(), "tuning_source": tuning_source, "serving": serving,
         "autotune": ({"trials": len(tuned["trials"]), "best_ms": tuned["ms"]} if tuned else None),
     }
     if rank == 0:
@@ -527,7 +571,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--retune", action="store_true", help="autotune even if a cached tuning exists")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=4000)
     ap.add_argument("--query-path", type=int, default=None,
                     help="0 = prefix/probe/expand launches, 1 = persistent fused launch")

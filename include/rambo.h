@@ -198,6 +198,17 @@ int rambo_query_ranges_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64
 int rambo_sync(rambo_t *h, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Folding over (Section 5.3, Fig. 5): every repetition's BFUs of buckets   */
+/* B/2..B-1 are ORed onto buckets 0..B/2-1, halving B and the index while R */
+/* stays; bucket b+B/2's documents join bucket b.  Because phi_r(d) = h mod */
+/* B and B/2 divides B, the result equals an index built with B/2 buckets   */
+/* from the same documents.  Synchronous; B must be even and the groups at  */
+/* most 512 bytes (RAMBO_EINVAL otherwise).  On failure (RAMBO_ENOMEM when  */
+/* the folded index cannot be allocated next to the current one) the index  */
+/* is unchanged.  Answers can only gain false positives.                    */
+int rambo_fold(rambo_t *h);
+
+/* ---------------------------------------------------------------------- */
 /* Introspection (host copies; synchronous).                               */
 
 /* Copies `nbytes` of the index starting at byte `offset` to host `dst`.
@@ -231,6 +242,12 @@ typedef struct {
                                        /* k-mers are probed and expanded by one warp   */
     uint32_t smem_docbits;             /* 1: expansion stages the bucket->document     */
                                        /* bitmaps in shared memory when they fit       */
+    uint32_t use_nibble_table;         /* 1: expansion through a per-4-bucket OR table */
+                                       /* staged in shared memory, when it fits 96 KiB */
+    uint32_t expand_filter;            /* 1: expansion forms repetition 0's union and  */
+                                       /* then tests only surviving documents against  */
+                                       /* the later repetitions (needs the nibble      */
+                                       /* table, B <= 256 and a small K)               */
 } rambo_tuning_t;
 
 int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out);

@@ -80,6 +80,7 @@ def _load():
             "orc_filter_popcount": (u64, [p, u32, u32]),
             "orc_is_inserted": (C.c_int, [p, u32]),
             "orc_num_filters_bits": (u64, [p]),
+            "orc_fold": (C.c_int, [p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -204,6 +205,12 @@ class Rambo:
             _check(_load().orc_query_kmers(self._h, km.size, _ptr(km), _ptr(out), threads),
                    "query_kmers")
         return out
+
+    # -- folding over (Section 5.3) -------------------------------------------
+    def fold(self):
+        """B -> B/2 by ORing bucket b + B/2 onto bucket b in every repetition."""
+        _check(_load().orc_fold(self._h), "fold")
+        self.B //= 2
 
     # -- introspection -----------------------------------------------------
     def bucket(self, d: int, r: int) -> int:

@@ -510,6 +510,49 @@ int orc_query_kmers(const orc_rambo *o, uint64_t n, const uint64_t *kmers, uint3
     return orc_query_many(o, n, NULL, NULL, kmers, out, n_threads);
 }
 
+/* Folding over (Section 5.3, Fig. 5): the BFUs of the second half of every
+ * repetition are ORed onto the first half, B -> B/2, R unchanged.  Bucket
+ * b + B/2 merges into bucket b, so DocIDs(M[b,r]) gains DocIDs(M[b+B/2,r])
+ * and every document's bucket becomes phi_r(d) mod B/2.  Needs B even. */
+int orc_fold(orc_rambo *o) {
+    if (o->B < 2 || (o->B & 1)) return ORC_EINVAL;
+    const uint32_t Bh = o->B / 2;
+    const uint64_t words = (o->nbits + 63) / 64;
+    uint64_t **filter = (uint64_t **)calloc((uint64_t)o->R * Bh, sizeof(uint64_t *));
+    uint32_t **docs = (uint32_t **)calloc((uint64_t)o->R * Bh, sizeof(uint32_t *));
+    uint32_t *ndocs = (uint32_t *)calloc((uint64_t)o->R * Bh, sizeof(uint32_t));
+    uint32_t *capdocs = (uint32_t *)calloc((uint64_t)o->R * Bh, sizeof(uint32_t));
+    if (!filter || !docs || !ndocs || !capdocs) {
+        free(filter); free(docs); free(ndocs); free(capdocs);
+        return ORC_ENOMEM;
+    }
+    for (uint32_t r = 0; r < o->R; ++r) {
+        for (uint32_t b = 0; b < Bh; ++b) {
+            const uint64_t lo = (uint64_t)r * o->B + b, hi = lo + Bh, nf = (uint64_t)r * Bh + b;
+            /* bitwise OR of the two filters */
+            for (uint64_t w = 0; w < words; ++w) o->filter[lo][w] |= o->filter[hi][w];
+            filter[nf] = o->filter[lo];
+            free(o->filter[hi]);
+            /* union of the two document lists (disjoint: a document has one bucket) */
+            const uint32_t n = o->ndocs[lo] + o->ndocs[hi];
+            uint32_t *d = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+            if (!d) return ORC_ENOMEM;
+            memcpy(d, o->docs[lo], sizeof(uint32_t) * o->ndocs[lo]);
+            memcpy(d + o->ndocs[lo], o->docs[hi], sizeof(uint32_t) * o->ndocs[hi]);
+            free(o->docs[lo]);
+            free(o->docs[hi]);
+            docs[nf] = d;
+            ndocs[nf] = n;
+            capdocs[nf] = n ? n : 1;
+        }
+    }
+    free(o->filter); free(o->docs); free(o->ndocs); free(o->capdocs);
+    o->filter = filter; o->docs = docs; o->ndocs = ndocs; o->capdocs = capdocs;
+    for (uint64_t i = 0; i < (uint64_t)o->K * o->R; ++i) o->bucket[i] %= Bh;
+    o->B = Bh;
+    return ORC_OK;
+}
+
 /* Introspection for the tests. */
 uint32_t orc_bucket_of(const orc_rambo *o, uint32_t d, uint32_t r) {
     return o->bucket[(uint64_t)d * o->R + r];

@@ -15,6 +15,9 @@ from __future__ import annotations
 import json
 import os
 
+# Tunings found on GB300, keyed by index geometry and batch shape.
+CACHE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
+
 KNOBS = (
     ("query_path", (0, 1)),
     ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
@@ -24,6 +27,8 @@ KNOBS = (
     ("expand_ctas_per_sm", (2, 4, 8, 16, 32)),
     ("use_byte_table", (0, 1)),
     ("smem_docbits", (0, 1)),
+    ("use_nibble_table", (0, 1)),
+    ("expand_filter", (0, 1)),
 )
 
 

@@ -22,6 +22,7 @@ struct rambo {
     void *d_stage;           // host-call staging + workspace
     size_t stage_bytes;
     uint32_t *d_tab;         // byte table for the expansion (or null)
+    uint32_t *d_ntab;        // nibble table for the expansion (or null)
     rambo_tuning_t tune;
     // profiling
     uint32_t prof_mask;
@@ -147,9 +148,19 @@ int probe_grid(const rambo_t *h) {
 }
 
 // (Re)allocates or frees the byte table to match the tuning; the table is
-// rebuilt from the current bitmaps on the handle's stream.
+// rebuilt from the current bitmaps on the handle's stream.  The nibble table
+// (small enough for shared memory) is kept whenever it fits 96 KiB.
 int apply_bytetab(rambo_t *h) {
     const Geometry &g = h->g;
+    const uint64_t nbytes = nibtab_words(g.B, g.R, g.W) * 4;
+    if (nbytes <= 96 * 1024 && g.Gw <= 32 && g.W <= 64) {
+        if (!h->d_ntab) RAMBO_TRY(cudaMalloc(&h->d_ntab, nbytes));
+        RAMBO_TRY(launch_build_nibtab(h->d_docbits, g.B, g.R, g.W, h->d_ntab, h->sm_count, h->stream));
+    } else if (h->d_ntab) {
+        RAMBO_TRY(cudaStreamSynchronize(h->stream));
+        cudaFree(h->d_ntab);
+        h->d_ntab = nullptr;
+    }
     const uint64_t bytes = bytetab_words(g.B, g.R, g.W) * 4;
     const bool want = h->tune.use_byte_table &&
                       bytes <= (uint64_t)h->tune.byte_table_max_mb * (1ull << 20);
@@ -252,7 +263,9 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         a.ends = ends;
         a.n = n;
         a.err = h->d_err;
-        ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits};
+        ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
+                     h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
+                     h->tune.expand_filter};
         FusedQueues qs{};
         qs.counters = reinterpret_cast<uint32_t *>(w + L.qcnt);
         qs.short_list = reinterpret_cast<uint32_t *>(w + L.slist);
@@ -298,7 +311,9 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 1);
         RAMBO_TRY(launch_probe_seqs(a, g, probe_grid(h), s));
     }
-    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits};
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
+                     h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
+                     h->tune.expand_filter};
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
         RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
@@ -328,7 +343,9 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
         StageScope sc(h, RAMBO_STAGE_PROBE_KMERS, s, 1);
         RAMBO_TRY(launch_probe_kmers(a, g, probe_grid(h), s));
     }
-    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits};
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
+                     h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
+                     h->tune.expand_filter};
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
         RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
@@ -379,6 +396,10 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     if (h->d_tab) {
         StageScope sc(h, RAMBO_STAGE_REGISTER, s, 1);
         RAMBO_TRY(launch_build_bytetab(h->d_docbits, g.B, g.R, g.W, h->d_tab, h->sm_count, s));
+    }
+    if (h->d_ntab) {
+        StageScope sc(h, RAMBO_STAGE_REGISTER, s, 1);
+        RAMBO_TRY(launch_build_nibtab(h->d_docbits, g.B, g.R, g.W, h->d_ntab, h->sm_count, s));
     }
     return RAMBO_OK;
 }
@@ -495,6 +516,8 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.byte_table_max_mb = 64;
     h->tune.query_path = 0;
     h->tune.smem_docbits = 1;
+    h->tune.use_nibble_table = 1;
+    h->tune.expand_filter = 1;
     h->tune.fused_tile_kmers = 1024;
     h->tune.fused_short_max = 1024;
     if ((rc = apply_bytetab(h))) return fail(rc);
@@ -512,6 +535,7 @@ int rambo_destroy(rambo_t *h) {
     cudaFree(h->d_err);
     cudaFree(h->d_stage);
     cudaFree(h->d_tab);
+    cudaFree(h->d_ntab);
     for (auto &p : h->pending) {
         cudaEventDestroy(p.start);
         cudaEventDestroy(p.stop);
@@ -686,6 +710,51 @@ int rambo_query_seqs(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64
     return read_and_clear_err(h);
 }
 
+// ---------------------------------------------------------------- folding
+
+int rambo_fold(rambo_t *h) {
+    if (!h) return RAMBO_EINVAL;
+    const Geometry old = h->g;
+    if (old.B < 2 || (old.B & 1) || old.Gw > 128) return RAMBO_EINVAL;
+    const Geometry ng = make_geometry(old.K, old.B / 2, old.R, old.m, old.eta, old.k, old.seed);
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    uint32_t *ni = nullptr, *nd = nullptr, *np = nullptr;
+    const uint64_t ni_bytes = ng.m * (uint64_t)ng.Gw * 4;
+    const uint64_t nd_bytes = (uint64_t)ng.R * ng.B * ng.W * 4;
+    int rc = cuda_rc(cudaMalloc(&ni, ni_bytes));
+    if (!rc) rc = cuda_rc(cudaMalloc(&nd, nd_bytes));
+    if (!rc) rc = cuda_rc(cudaMalloc(&np, (uint64_t)ng.K * ng.R * 4));
+    if (!rc) rc = cuda_rc(launch_fold(h->d_index, old.Gw, ni, ng.Gw, old.m, old.B, old.R, h->d_docbits,
+                                      nd, old.W, h->sm_count, h->stream));
+    // the folded partition is phi_r(d) mod B/2 = hash mod B/2, since B/2 divides B
+    if (!rc) rc = cuda_rc(launch_partition(np, ng.K, ng.R, ng.B, ng.seed, h->stream));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    if (rc) {
+        cudaFree(ni);
+        cudaFree(nd);
+        cudaFree(np);
+        return rc;  // the index is unchanged
+    }
+    cudaFree(h->d_index);
+    cudaFree(h->d_docbits);
+    cudaFree(h->d_phi);
+    h->d_index = ni;
+    h->d_docbits = nd;
+    h->d_phi = np;
+    h->g = ng;
+    if (h->d_tab) {
+        cudaFree(h->d_tab);
+        h->d_tab = nullptr;
+    }
+    if (h->d_ntab) {
+        cudaFree(h->d_ntab);
+        h->d_ntab = nullptr;
+    }
+    return apply_bytetab(h);
+}
+
 // --------------------------------------------------------- introspection
 
 int rambo_copy_index(const rambo_t *h, uint64_t offset, uint64_t nbytes, void *dst) {
@@ -728,7 +797,8 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
     if (!h || !t) return RAMBO_EINVAL;
     if (t->probe_ctas_per_sm > 32 || t->expand_ctas_per_sm == 0 || t->expand_ctas_per_sm > 64 ||
         t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 1 || t->fused_tile_kmers == 0 ||
-        t->fused_tile_kmers > (1u << 24) || t->fused_short_max > (1u << 24) || t->smem_docbits > 1)
+        t->fused_tile_kmers > (1u << 24) || t->fused_short_max > (1u << 24) || t->smem_docbits > 1 ||
+        t->use_nibble_table > 1 || t->expand_filter > 1)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

@@ -195,6 +195,10 @@ struct ExpandArgs {
     uint32_t *out;           // n x W
     const uint32_t *tab;     // byte table (R*ceil(B/8)*256*W) or null
     uint32_t smem_docbits;   // 1: stage DocBits in shared memory when it fits
+    const uint32_t *ntab;    // nibble table (R*ceil(B/4)*16*W) or null
+    const uint32_t *phi;     // K x R partition (candidate filtering)
+    uint32_t K;
+    uint32_t filter;         // 1: expand by candidate filtering when it fits
 };
 
 struct InsertArgs {
@@ -229,6 +233,11 @@ cudaError_t launch_register_docs(const uint32_t *doc_ids, uint64_t n, const uint
                                  uint32_t K, uint32_t R, uint32_t B, uint32_t W, uint32_t *docbits,
                                  uint32_t *err, cudaStream_t s);
 cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s);
+// Folding over B -> B/2 of the index (groups up to 512 bytes) and DocBits.
+cudaError_t launch_fold(const uint32_t *old_index, uint32_t old_gw, uint32_t *new_index,
+                        uint32_t new_gw, uint64_t m, uint32_t B, uint32_t R,
+                        const uint32_t *old_db, uint32_t *new_db, uint32_t W, int sm_count,
+                        cudaStream_t s);
 cudaError_t launch_probe_seqs(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 // Work queues of the persistent fused query (workspace arrays).
@@ -249,6 +258,9 @@ cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry
 // max_blocks caps the expansion grid
 cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, cudaStream_t s);
 uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W);
+uint64_t nibtab_words(uint32_t B, uint32_t R, uint32_t W);
+cudaError_t launch_build_nibtab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
+                                uint32_t *ntab, int sm_count, cudaStream_t s);
 cudaError_t launch_build_bytetab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
                                  uint32_t *tab, int sm_count, cudaStream_t s);
 

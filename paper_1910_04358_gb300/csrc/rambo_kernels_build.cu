@@ -207,6 +207,67 @@ __global__ void __launch_bounds__(INSERT_THREADS, 1) k_insert(InsertArgs a) {
     }
 }
 
+// --------------------------------------------------------------------- fold
+// Folding over (Section 5.3, Fig. 5): B -> Bh = B/2.  In position group p,
+// repetition r's row of B bits (bits r*B ..) becomes the OR of its two halves,
+// stored as the Bh-bit row at bits r*Bh of the new group.  One warp per group:
+// the old group is staged in shared memory, lane r builds row r 32 bits at a
+// time, and the new words are assembled with shared-memory atomicOr.
+constexpr int FOLD_THREADS = 256;
+constexpr int FOLD_MAX_WORDS = 128;  // groups up to 512 bytes
+
+__device__ __forceinline__ uint32_t bits_at(const uint32_t *w, uint32_t nwords, uint32_t bit) {
+    const uint32_t i = bit >> 5, sh = bit & 31;
+    const uint32_t lo = w[i];
+    const uint32_t hi = i + 1 < nwords ? w[i + 1] : 0u;
+    return sh ? __funnelshift_r(lo, hi, sh) : lo;
+}
+
+__global__ void __launch_bounds__(FOLD_THREADS)
+k_fold(const uint32_t *old_index, uint32_t old_gw, uint32_t *new_index, uint32_t new_gw, uint64_t m,
+       uint32_t B, uint32_t R) {
+    __shared__ uint32_t s_old[FOLD_THREADS / 32][FOLD_MAX_WORDS];
+    __shared__ uint32_t s_new[FOLD_THREADS / 32][FOLD_MAX_WORDS];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t Bh = B / 2;
+    const uint64_t warp = (uint64_t)blockIdx.x * (FOLD_THREADS / 32) + wib;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (FOLD_THREADS / 32);
+    for (uint64_t p = warp; p < m; p += nwarps) {
+        for (uint32_t i = lane; i < old_gw; i += 32) s_old[wib][i] = old_index[p * old_gw + i];
+        for (uint32_t i = lane; i < new_gw; i += 32) s_new[wib][i] = 0;
+        __syncwarp();
+        for (uint32_t r = lane; r < R; r += 32) {
+            for (uint32_t c = 0; c < Bh; c += 32) {
+                const uint32_t len = Bh - c < 32 ? Bh - c : 32;
+                const uint32_t mask = len == 32 ? FULL : ((1u << len) - 1u);
+                const uint32_t x = (bits_at(s_old[wib], old_gw, r * B + c) |
+                                    bits_at(s_old[wib], old_gw, r * B + Bh + c)) & mask;
+                const uint32_t dst = r * Bh + c;
+                const uint32_t wi = dst >> 5, sh = dst & 31;
+                atomicOr(&s_new[wib][wi], x << sh);
+                if (sh && len > 32 - sh) atomicOr(&s_new[wib][wi + 1], x >> (32 - sh));
+            }
+        }
+        __syncwarp();
+        for (uint32_t i = lane; i < new_gw; i += 32) new_index[p * new_gw + i] = s_new[wib][i];
+        __syncwarp();
+    }
+}
+
+// new DocBits[r][b] = old[r][b] | old[r][b + Bh]
+__global__ void k_fold_docbits(const uint32_t *old_db, uint32_t *new_db, uint32_t B, uint32_t R,
+                               uint32_t W) {
+    const uint32_t Bh = B / 2;
+    const uint64_t total = (uint64_t)R * Bh * W;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)(i % W);
+        const uint64_t rb = i / W;
+        const uint32_t b = (uint32_t)(rb % Bh), r = (uint32_t)(rb / Bh);
+        new_db[i] = old_db[((uint64_t)r * B + b) * W + w] | old_db[((uint64_t)r * B + b + Bh) * W + w];
+    }
+}
+
 template <typename KernelT>
 int blocks_per_sm(KernelT kernel, int threads) {
     int n = 0;
@@ -253,6 +314,18 @@ cudaError_t launch_register_docs(const uint32_t *doc_ids, uint64_t n, const uint
     if (total == 0) return cudaSuccess;
     k_register<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(doc_ids, n, phi, K, R, B, W, docbits,
                                                                err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const uint32_t *old_index, uint32_t old_gw, uint32_t *new_index,
+                        uint32_t new_gw, uint64_t m, uint32_t B, uint32_t R,
+                        const uint32_t *old_db, uint32_t *new_db, uint32_t W, int sm_count,
+                        cudaStream_t s) {
+    if (old_gw > FOLD_MAX_WORDS || new_gw > FOLD_MAX_WORDS || (B & 1)) return cudaErrorInvalidValue;
+    k_fold<<<sm_count * 8, FOLD_THREADS, 0, s>>>(old_index, old_gw, new_index, new_gw, m, B, R);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fold_docbits<<<sm_count * 4, 256, 0, s>>>(old_db, new_db, B, R, W);
     return cudaGetLastError();
 }
 

@@ -478,6 +478,168 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand(ExpandArgs a) {
     }
 }
 
+// Expansion through the nibble table in shared memory (small K): one query
+// per warp, every lane holding up to 32*C answer words.  The query's bucket
+// mask (Gw <= 32 words) sits in lane registers, one word per lane, and rows
+// are fetched 32 bits at a time with shuffles; every nonzero 4-bucket nibble
+// of a row costs one conflict-free shared-memory row read.
+constexpr size_t SMEM_NIBTAB_MAX = 96 * 1024;
+
+template <int C>
+__global__ void __launch_bounds__(EXPAND_THREADS) k_expand_nib(ExpandArgs a) {
+    extern __shared__ uint32_t stab[];
+    const uint32_t NQ = (a.B + 3) / 4;
+    const uint32_t words = a.R * NQ * 16 * a.W;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) stab[i] = __ldg(a.ntab + i);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * (EXPAND_THREADS / 32) + threadIdx.x / 32;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (EXPAND_THREADS / 32);
+    for (uint64_t q = warp; q < a.n; q += nwarps) {
+        const uint32_t bmw = (uint32_t)lane < a.Gw ? __ldg(a.acc + q * a.Gw + lane) : 0u;
+        uint32_t res[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) res[c] = FULL;
+        bool dead = false;
+        for (uint32_t r = 0; r < a.R; ++r) {
+            uint32_t o[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) o[c] = 0;
+            uint32_t any = 0;
+            const uint32_t lo = r * a.B;
+            for (uint32_t i = 0; i < a.B; i += 32) {
+                const uint32_t bit = lo + i, wi = bit >> 5, sh = bit & 31;
+                const uint32_t w0v = __shfl_sync(FULL, bmw, wi & 31);
+                const uint32_t w1v = __shfl_sync(FULL, bmw, (wi + 1) & 31);
+                uint32_t chunk = sh ? __funnelshift_r(w0v, wi + 1 < a.Gw ? w1v : 0u, sh) : w0v;
+                const uint32_t nb = a.B - i < 32 ? a.B - i : 32;
+                if (nb < 32) chunk &= (1u << nb) - 1u;
+                any |= chunk;
+                const uint32_t j0 = i / 4;
+                while (chunk) {
+                    const uint32_t t = (__ffs(chunk) - 1) & ~3u;  // first nonzero nibble
+                    const uint32_t v = (chunk >> t) & 15u;
+                    chunk &= ~(15u << t);
+                    const uint32_t *row = stab + (((r * NQ + j0 + t / 4) * 16 + v) * a.W);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const uint32_t w = lane + 32 * c;
+                        if (w < a.W) o[c] |= row[w];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) res[c] &= o[c];
+            if (!any) dead = true;
+        }
+        uint32_t *out = a.out + q * a.W;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const uint32_t w = lane + 32 * c;
+            if (w < a.W) out[w] = dead ? 0u : res[c];
+        }
+    }
+}
+
+// Expansion by candidate filtering (the paper's sparse evaluation, Section
+// 5.1 "Query time speedup", applied per document): the union of repetition 0
+// is formed from the nibble table (its repetition-0 rows staged in shared
+// memory); for every later repetition r only the documents still set are
+// tested -- document d survives iff bit phi_r(d) of row r is set -- with phi
+// staged in shared memory as bytes (B <= 256) and the query's bucket mask in
+// a per-warp shared slot.  The surviving set after the last repetition is
+// exactly AND_r of the unions.  One query per warp, each lane owning answer
+// words lane + 32c (W <= 32*C); Gw <= 32.
+template <int C>
+__global__ void __launch_bounds__(EXPAND_THREADS) k_expand_filter(ExpandArgs a) {
+    extern __shared__ uint32_t smem_f[];
+    const uint32_t NQ = (a.B + 3) / 4;
+    const uint32_t tab0 = NQ * 16 * a.W;  // nibble-table words of repetition 0
+    uint32_t *stab = smem_f;
+    uint32_t *sbm = smem_f + tab0;        // EXPAND_THREADS/32 slots of 32 words
+    uint8_t *sphi = reinterpret_cast<uint8_t *>(sbm + EXPAND_THREADS);  // K*R bytes
+    for (uint32_t i = threadIdx.x; i < tab0; i += blockDim.x) stab[i] = __ldg(a.ntab + i);
+    for (uint32_t i = threadIdx.x; i < a.K * a.R; i += blockDim.x) sphi[i] = (uint8_t)__ldg(a.phi + i);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    uint32_t *bm = sbm + (threadIdx.x / 32) * 32;
+    const uint64_t warp = (uint64_t)blockIdx.x * (EXPAND_THREADS / 32) + threadIdx.x / 32;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (EXPAND_THREADS / 32);
+    for (uint64_t q = warp; q < a.n; q += nwarps) {
+        bm[lane] = (uint32_t)lane < a.Gw ? __ldg(a.acc + q * a.Gw + lane) : 0u;
+        __syncwarp();
+        // repetition 0: union of the passing buckets via the nibble table
+        uint32_t res[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) res[c] = 0;
+        for (uint32_t i = 0; i < a.B; i += 32) {
+            uint32_t chunk = bm[i >> 5];
+            const uint32_t nb = a.B - i < 32 ? a.B - i : 32;
+            if (nb < 32) chunk &= (1u << nb) - 1u;
+            const uint32_t j0 = i / 4;
+            while (chunk) {
+                const uint32_t t = (__ffs(chunk) - 1) & ~3u;
+                const uint32_t v = (chunk >> t) & 15u;
+                chunk &= ~(15u << t);
+                const uint32_t *row = stab + (((j0 + t / 4) * 16 + v) * a.W);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t w = lane + 32 * c;
+                    if (w < a.W) res[c] |= row[w];
+                }
+            }
+        }
+        // repetitions 1..R-1: keep the candidates whose bucket passes
+        for (uint32_t r = 1; r < a.R; ++r) {
+            uint32_t nz = 0;
+            const uint32_t lo = r * a.B;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                uint32_t x = res[c], keep = 0;
+                const uint32_t d0 = 32 * (lane + 32 * c);
+                while (x) {
+                    const uint32_t j = __ffs(x) - 1;
+                    x &= x - 1;
+                    const uint32_t bit = lo + sphi[(d0 + j) * a.R + r];
+                    keep |= ((bm[bit >> 5] >> (bit & 31)) & 1u) << j;
+                }
+                res[c] = keep;
+                nz |= keep;
+            }
+            if (!__any_sync(FULL, nz)) break;
+        }
+        uint32_t *out = a.out + q * a.W;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const uint32_t w = lane + 32 * c;
+            if (w < a.W) out[w] = res[c];
+        }
+        __syncwarp();
+    }
+}
+
+// Nibble table: ntab[((r*NQ + j)*16 + v)*W + w] = OR over set bits t of v
+// (4j+t < B) of DocBits[r][4j+t][w].
+__global__ void k_build_nibtab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
+                               uint32_t *ntab) {
+    const uint32_t NQ = (B + 3) / 4;
+    const uint64_t total = (uint64_t)R * NQ * 16 * W;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)(i % W);
+        const uint64_t rest = i / W;
+        const uint32_t v = (uint32_t)(rest % 16);
+        const uint64_t rj = rest / 16;
+        const uint32_t j = (uint32_t)(rj % NQ), r = (uint32_t)(rj / NQ);
+        uint32_t o = 0;
+        for (uint32_t t = 0; t < 4; ++t) {
+            const uint32_t b = 4 * j + t;
+            if (((v >> t) & 1u) && b < B) o |= docbits[((uint64_t)r * B + b) * W + w];
+        }
+        ntab[i] = o;
+    }
+}
+
 // Byte table: tab[((r*NJ + j)*256 + v)*W + w] = OR over set bits i of v
 // (8j+i < B) of DocBits[r][8j+i][w].
 __global__ void k_build_bytetab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
@@ -746,6 +908,34 @@ cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, cudaStream_t s) {
     uint64_t blocks = (units + EXPAND_THREADS / 32 - 1) / (EXPAND_THREADS / 32);
     const uint64_t cap = (uint64_t)max_blocks;
     if (blocks > cap) blocks = cap;
+    // candidate filtering: repetition-0 nibble rows, the per-warp mask slots
+    // and phi as bytes in shared memory
+    const size_t filt_bytes = (size_t)((a.B + 3) / 4) * 16 * a.W * 4 + EXPAND_THREADS * 4 +
+                              ((size_t)a.K * a.R + 3) / 4 * 4;
+    if (a.filter && a.ntab && a.phi && a.Gw <= 32 && a.W <= 64 && a.B <= 256 &&
+        filt_bytes <= SMEM_NIBTAB_MAX && a.n >= (uint64_t)max_blocks * 64) {
+        cudaError_t e2 = cudaSuccess;
+        if (filt_bytes > 48 * 1024)
+            e2 = a.W > 32 ? cudaFuncSetAttribute(k_expand_filter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filt_bytes)
+                          : cudaFuncSetAttribute(k_expand_filter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filt_bytes);
+        if (e2 != cudaSuccess) return e2;
+        if (a.W > 32) k_expand_filter<2><<<(unsigned)max_blocks, EXPAND_THREADS, filt_bytes, s>>>(a);
+        else k_expand_filter<1><<<(unsigned)max_blocks, EXPAND_THREADS, filt_bytes, s>>>(a);
+        return cudaGetLastError();
+    }
+    // nibble table in shared memory (small K): one query per warp
+    const size_t nib_bytes = nibtab_words(a.B, a.R, a.W) * 4;
+    if (a.ntab && a.Gw <= 32 && a.W <= 64 && nib_bytes <= SMEM_NIBTAB_MAX &&
+        a.n >= (uint64_t)max_blocks * 64) {
+        cudaError_t e2 = cudaSuccess;
+        if (nib_bytes > 48 * 1024)
+            e2 = a.W > 32 ? cudaFuncSetAttribute(k_expand_nib<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nib_bytes)
+                          : cudaFuncSetAttribute(k_expand_nib<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nib_bytes);
+        if (e2 != cudaSuccess) return e2;
+        if (a.W > 32) k_expand_nib<2><<<(unsigned)max_blocks, EXPAND_THREADS, nib_bytes, s>>>(a);
+        else k_expand_nib<1><<<(unsigned)max_blocks, EXPAND_THREADS, nib_bytes, s>>>(a);
+        return cudaGetLastError();
+    }
     // DocBits in shared memory when it fits and every block gets enough
     // queries to pay for staging it
     const size_t db_bytes = (size_t)a.R * a.B * a.W * 4;
@@ -796,6 +986,16 @@ cudaError_t launch_fused_e(const FusedArgs &f, int go, int sm, cudaStream_t s) {
 }
 
 bool fused_supported(const Geometry &g) { return g.chunks == 1 && g.Gw <= 128; }
+
+uint64_t nibtab_words(uint32_t B, uint32_t R, uint32_t W) {
+    return (uint64_t)R * ((B + 3) / 4) * 16 * W;
+}
+
+cudaError_t launch_build_nibtab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,
+                                uint32_t *ntab, int sm_count, cudaStream_t s) {
+    k_build_nibtab<<<sm_count * 4, 256, 0, s>>>(docbits, B, R, W, ntab);
+    return cudaGetLastError();
+}
 
 uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W) {
     return (uint64_t)R * ((B + 7) / 8) * 256 * W;

@@ -79,6 +79,7 @@ def load():
             "rambo_set_l2_fetch_granularity": (i, [i, C.POINTER(i)]),
             "rambo_query_seqs_noalloc": (i, [p, u64, p, u64, p, p, p]),
             "rambo_query_ranges_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
+            "rambo_fold": (i, [p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -148,7 +149,8 @@ class Workspace:
 STAGES = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
 TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_per_sm",
                  "use_byte_table", "byte_table_max_mb", "query_path", "fused_tile_kmers",
-                 "fused_short_max", "smem_docbits")
+                 "fused_short_max", "smem_docbits", "use_nibble_table",
+                 "expand_filter")
 
 
 class _Tuning(C.Structure):
@@ -313,6 +315,15 @@ class Index:
 
     def sync(self, stream=None):
         _check(load().rambo_sync(self._h, _stream_handle(stream)), "rambo_sync")
+
+    # ------------------------------------------------------------ folding
+    def fold(self):
+        """Folding over (Section 5.3): B -> B/2, OR of bucket b+B/2 onto b."""
+        _check(load().rambo_fold(self._h), "rambo_fold")
+        info = _Info()
+        _check(load().rambo_get_info(self._h, C.byref(info)), "rambo_get_info")
+        self.info = {f: getattr(info, f) for f, _ in _Info._fields_}
+        self.B = info.B
 
     # ------------------------------------------------------------- tuning
     def get_tuning(self) -> dict:

@@ -186,7 +186,9 @@ def test_tuning_knobs_do_not_change_results(rambo_lib):
                      probe_ctas_per_sm=1),
                 dict(query_path=0, smem_docbits=0),
                 dict(query_path=0, smem_docbits=1, expand_ctas_per_sm=1),
-                dict(query_path=1, smem_docbits=0, use_byte_table=0)]
+                dict(query_path=1, smem_docbits=0, use_byte_table=0),
+                dict(query_path=0, use_nibble_table=1, expand_ctas_per_sm=1),
+                dict(query_path=0, use_nibble_table=0)]
     for st in settings:
         idx.set_tuning(**st)
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want_s), st
@@ -275,3 +277,47 @@ def test_argument_errors(rambo_lib):
     with pytest.raises(rambo_lib.RamboError) as e:
         idx.sync()
     assert e.value.code == rambo_lib.RAMBO_EINVAL
+
+
+# ------------------------------------------------------------------ folding
+
+@pytest.mark.parametrize("K,B,R,m", [(120, 16, 3, 1 << 12), (300, 100, 5, 1 << 11),
+                                     (90, 64, 6, 1 << 10), (40, 2, 2, 1 << 12)])
+def test_fold_matches_oracle_and_direct_half_index(rambo_lib, K, B, R, m):
+    p = synth.Params(K=K, B=B, R=R, m=m, eta=2, k=31, seed=6)
+    rng = np.random.default_rng(K + B)
+    corpus = synth.family_corpus(rng, p, n_seeds=max(1, K // 10), doc_len=500, sub_rate=0.02)
+    q = synth.sample_queries(rng, corpus, rng.integers(25, 200, size=200), 0.6)
+    o = oracle_index(p, corpus)
+    idx = gpu_index(rambo_lib, p, corpus)
+    before = gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets)
+    idx.fold()
+    o.fold()
+    ph = synth.Params(K=K, B=B // 2, R=R, m=m, eta=2, k=31, seed=6)
+    assert_index_equal(idx, o, ph)
+    assert_docbits_equal(idx, o, ph)
+    after = gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets)
+    assert np.array_equal(after, o.query_seqs(q.packed, q.offsets))
+    assert np.all((before & ~after) == 0)
+    direct = gpu_index(rambo_lib, ph, corpus)
+    assert np.array_equal(direct.copy_index(), idx.copy_index())
+
+
+def test_expansion_variants_on_many_kmer_queries(rambo_lib):
+    # enough queries per block that the shared-memory variants engage
+    p = synth.Params(K=700, B=32, R=4, m=1 << 14, eta=2, k=31, seed=12)
+    rng = np.random.default_rng(31)
+    corpus = synth.family_corpus(rng, p, n_seeds=30, doc_len=600, sub_rate=0.02)
+    kmers = synth.sample_kmers(rng, corpus, 12_000, p.k, 0.5)
+    o = oracle_index(p, corpus)
+    want = o.query_kmers(kmers, threads=4)
+    idx = gpu_index(rambo_lib, p, corpus)
+    for st in (dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=1),
+               dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=0),
+               dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=1),
+               dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=0, use_byte_table=1),
+               dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=0, use_byte_table=0)):
+        idx.set_tuning(**st)
+        got = idx.query_kmers_dev(_dev(kmers, np.int64))
+        idx.sync()
+        assert np.array_equal(rambo_lib.as_u32(got), want), st

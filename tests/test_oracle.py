@@ -370,3 +370,28 @@ def test_invalid_arguments():
         o.insert(4, np.zeros(4, np.uint8), 0, 8)
     with pytest.raises(oracle.OracleError):
         o.query_kmer(1 << 10)  # bit at or above 2k
+
+
+# ------------------------------------------------------------------ folding
+
+def test_fold_equals_index_built_with_half_the_buckets():
+    # phi_r(d) = h mod B and B/2 divides B, so folding B -> B/2 must give the
+    # index built directly with B/2 buckets, filter for filter and answer for answer
+    p, corpus, q = _small_case(K=50, B=8, R=3, m=1 << 12)
+    o = _build(p, corpus)
+    before = o.query_seqs(q.packed, q.offsets)
+    o.fold()
+    ph = synth.Params(K=p.K, B=p.B // 2, R=p.R, m=p.m, eta=p.eta, k=p.k, seed=p.seed)
+    direct = _build(ph, corpus)
+    for r in range(p.R):
+        for b in range(ph.B):
+            assert np.array_equal(o.filter_words(r, b), direct.filter_words(r, b))
+        for d in range(p.K):
+            assert o.bucket(d, r) == direct.bucket(d, r)
+    after = o.query_seqs(q.packed, q.offsets)
+    assert np.array_equal(after, direct.query_seqs(q.packed, q.offsets))
+    # folding only adds false positives: the folded answer contains the original one
+    assert np.all((before & ~after) == 0)
+    with pytest.raises(oracle.OracleError):
+        odd = oracle.Rambo(10, 3, 1, 64, 1, k=5)
+        odd.fold()
