@@ -248,6 +248,12 @@ typedef struct {
                                        /* then tests only surviving documents against  */
                                        /* the later repetitions (needs the nibble      */
                                        /* table, B <= 256 and a small K)               */
+    uint32_t early_exit;               /* path 1: stop probing a query once one of its */
+                                       /* repetition rows is empty (its answer is then */
+                                       /* empty; Section 3.3.1 "the first FALSE is     */
+                                       /* conclusive", Section 5.1 RAMBO+).  Off by    */
+                                       /* default: every k-mer is probed               */
+    uint32_t early_exit_segment;       /* k-mers between checks (multiple of 128)      */
 } rambo_tuning_t;
 
 int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out);
@@ -298,6 +304,10 @@ int rambo_profile_reset(rambo_t *h, uint32_t stage_mask);
 
 /* Waits for every recorded event, then copies the counters to *out. */
 int rambo_profile_read(rambo_t *h, rambo_profile_t *out);
+
+/* k-mers the fused path actually probed while early_exit was on (waits for
+ * the device); reset != 0 zeroes the counter afterwards. */
+int rambo_probed_kmers(rambo_t *h, uint64_t *out, int reset);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,7 @@ struct rambo {
     uint32_t *d_docbits;     // R * B * W words
     uint32_t *d_phi;         // K * R
     uint32_t *d_err;         // latched device error bits
+    unsigned long long *d_probed;  // k-mers probed under early exit
     void *d_stage;           // host-call staging + workspace
     size_t stage_bytes;
     uint32_t *d_tab;         // byte table for the expansion (or null)
@@ -274,6 +275,9 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         qs.tile = h->tune.fused_tile_kmers;
         qs.short_max = h->tune.fused_short_max;
         qs.user_bases = packed_bytes * 4;
+        qs.early_exit = h->tune.early_exit;
+        qs.segment = h->tune.early_exit_segment;
+        qs.probed = h->d_probed;
         {
             StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
             RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s,
@@ -504,6 +508,8 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     if ((rc = cuda_rc(cudaMalloc(&h->d_docbits, docbits_bytes)))) return fail(rc);
     if ((rc = cuda_rc(cudaMalloc(&h->d_phi, (uint64_t)K * R * 4)))) return fail(rc);
     if ((rc = cuda_rc(cudaMalloc(&h->d_err, 4)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&h->d_probed, 8)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemsetAsync(h->d_probed, 0, 8, h->stream)))) return fail(rc);
     if ((rc = cuda_rc(cudaMemsetAsync(h->d_index, 0, index_bytes, h->stream)))) return fail(rc);
     if ((rc = cuda_rc(cudaMemsetAsync(h->d_docbits, 0, docbits_bytes, h->stream)))) return fail(rc);
     if ((rc = cuda_rc(cudaMemsetAsync(h->d_err, 0, 4, h->stream)))) return fail(rc);
@@ -518,6 +524,8 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.smem_docbits = 1;
     h->tune.use_nibble_table = 1;
     h->tune.expand_filter = 1;
+    h->tune.early_exit = 0;
+    h->tune.early_exit_segment = 256;
     h->tune.fused_tile_kmers = 1024;
     h->tune.fused_short_max = 1024;
     if ((rc = apply_bytetab(h))) return fail(rc);
@@ -533,6 +541,7 @@ int rambo_destroy(rambo_t *h) {
     cudaFree(h->d_docbits);
     cudaFree(h->d_phi);
     cudaFree(h->d_err);
+    cudaFree(h->d_probed);
     cudaFree(h->d_stage);
     cudaFree(h->d_tab);
     cudaFree(h->d_ntab);
@@ -798,13 +807,27 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
     if (t->probe_ctas_per_sm > 32 || t->expand_ctas_per_sm == 0 || t->expand_ctas_per_sm > 64 ||
         t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 1 || t->fused_tile_kmers == 0 ||
         t->fused_tile_kmers > (1u << 24) || t->fused_short_max > (1u << 24) || t->smem_docbits > 1 ||
-        t->use_nibble_table > 1 || t->expand_filter > 1)
+        t->use_nibble_table > 1 || t->expand_filter > 1 || t->early_exit > 1 ||
+        t->early_exit_segment == 0 || (t->early_exit_segment & 127) || t->early_exit_segment > (1u << 24))
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
     RAMBO_TRY(cudaStreamSynchronize(h->stream));
     h->tune = *t;
     return apply_bytetab(h);
+}
+
+int rambo_probed_kmers(rambo_t *h, uint64_t *out, int reset) {
+    if (!h || !out) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    unsigned long long v = 0;
+    RAMBO_TRY(cudaDeviceSynchronize());
+    RAMBO_TRY(cudaMemcpy(&v, h->d_probed, 8, cudaMemcpyDeviceToHost));
+    if (reset) RAMBO_TRY(cudaMemset(h->d_probed, 0, 8));
+    RAMBO_TRY(cudaDeviceSynchronize());
+    *out = v;
+    return RAMBO_OK;
 }
 
 int rambo_profile_reset(rambo_t *h, uint32_t stage_mask) {

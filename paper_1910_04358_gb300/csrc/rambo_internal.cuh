@@ -249,6 +249,9 @@ struct FusedQueues {
     uint32_t tile;           // k-mers per long tile
     uint32_t short_max;      // longest short query (k-mers)
     uint64_t user_bases;     // bases addressable from the caller's packed pointer
+    uint32_t early_exit;     // 1: skip the rest of a query once a repetition row is empty
+    uint32_t segment;        // early exit: k-mers between checks (multiple of 128)
+    unsigned long long *probed;  // early exit: k-mers actually probed (or null)
 };
 bool fused_supported(const Geometry &g);
 // p.acc is unused (the bucket masks of long queries are e.acc).

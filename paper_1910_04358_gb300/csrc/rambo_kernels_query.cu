@@ -493,6 +493,7 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand_nib(ExpandArgs a) {
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) stab[i] = __ldg(a.ntab + i);
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const uint32_t stride = 16 * a.W;  // words from one nibble position to the next
     const uint64_t warp = (uint64_t)blockIdx.x * (EXPAND_THREADS / 32) + threadIdx.x / 32;
     const uint64_t nwarps = (uint64_t)gridDim.x * (EXPAND_THREADS / 32);
     for (uint64_t q = warp; q < a.n; q += nwarps) {
@@ -501,30 +502,29 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand_nib(ExpandArgs a) {
 #pragma unroll
         for (int c = 0; c < C; ++c) res[c] = FULL;
         bool dead = false;
+        const uint32_t *tj = stab + lane;  // table row of (r, nibble position), this lane's word
         for (uint32_t r = 0; r < a.R; ++r) {
             uint32_t o[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) o[c] = 0;
             uint32_t any = 0;
-            const uint32_t lo = r * a.B;
             for (uint32_t i = 0; i < a.B; i += 32) {
-                const uint32_t bit = lo + i, wi = bit >> 5, sh = bit & 31;
+                const uint32_t bit = r * a.B + i, wi = bit >> 5, sh = bit & 31;
                 const uint32_t w0v = __shfl_sync(FULL, bmw, wi & 31);
                 const uint32_t w1v = __shfl_sync(FULL, bmw, (wi + 1) & 31);
                 uint32_t chunk = sh ? __funnelshift_r(w0v, wi + 1 < a.Gw ? w1v : 0u, sh) : w0v;
                 const uint32_t nb = a.B - i < 32 ? a.B - i : 32;
                 if (nb < 32) chunk &= (1u << nb) - 1u;
                 any |= chunk;
-                const uint32_t j0 = i / 4;
-                while (chunk) {
-                    const uint32_t t = (__ffs(chunk) - 1) & ~3u;  // first nonzero nibble
-                    const uint32_t v = (chunk >> t) & 15u;
-                    chunk &= ~(15u << t);
-                    const uint32_t *row = stab + (((r * NQ + j0 + t / 4) * 16 + v) * a.W);
+                // every nibble is looked up: value 0 selects the all-zero row
 #pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const uint32_t w = lane + 32 * c;
-                        if (w < a.W) o[c] |= row[w];
+                for (int t = 0; t < 8; ++t) {
+                    if (i + 4 * t < a.B) {
+                        const uint32_t *row = tj + ((chunk >> (4 * t)) & 15u) * a.W;
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            if (lane + 32 * c < (int)a.W) o[c] |= row[32 * c];
+                        tj += stride;
                     }
                 }
             }
@@ -692,7 +692,34 @@ struct FusedArgs {
     uint32_t short_max;          // k-mers of the longest short query
     uint64_t user_bases;         // bases addressable from the caller's pointer
     ExpandArgs e;                // acc = bucket masks of long queries
+    uint32_t early_exit;         // 1: stop probing a query once a repetition row is empty
+    uint32_t segment;            // early exit: k-mers between checks of a short query
+    unsigned long long *probed;  // early exit: k-mers actually probed (or null)
 };
+
+// True when some repetition's row of the bucket mask bm (shared memory) has
+// no bit set: the answer is then empty whatever the remaining k-mers give.
+__device__ __forceinline__ bool mask_dead(const uint32_t *bm, uint32_t Gw, uint32_t B, uint32_t R,
+                                          int lane) {
+    bool dead = false;
+    for (uint32_t r0 = 0; r0 < R; r0 += 32) {
+        const uint32_t r = r0 + lane;
+        bool empty = false;
+        if (r < R) {
+            empty = true;
+            for (uint32_t i = 0; i < B && empty; i += 32) {
+                const uint32_t bit = r * B + i, wi = bit >> 5, sh = bit & 31;
+                uint32_t chunk = bm[wi];
+                if (sh) chunk = __funnelshift_r(chunk, wi + 1 < Gw ? bm[wi + 1] : 0u, sh);
+                const uint32_t nb = B - i < 32 ? B - i : 32;
+                if (nb < 32) chunk &= (1u << nb) - 1u;
+                if (chunk) empty = false;
+            }
+        }
+        if (__any_sync(FULL, empty)) dead = true;
+    }
+    return dead;
+}
 
 __device__ __forceinline__ uint64_t fused_kmers(const FusedArgs &f, uint64_t q, uint64_t *start) {
     const uint64_t b0 = f.p.offsets[q], b1 = f.p.ends[q];
@@ -807,8 +834,18 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fused(FusedArgs f) {
         const uint64_t nk = fused_kmers(f, q, &start);
         const uint64_t k0 = (t - f.tile_prefix[q]) * f.tile;
         const uint64_t k1 = k0 + f.tile < nk ? k0 + f.tile : nk;
-        const Slice<SW> s = fused_probe_range<SW, LPG, ETA>(f.p, start, k0, k1, lane, word0);
-        if (sub == 0) flush_slice<SW>(const_cast<uint32_t *>(f.e.acc), q, f.p.Gw, word0, s);
+        bool skip = false;
+        if (f.early_exit) {  // a tile of an already-empty query changes nothing
+            for (uint32_t w = lane; w < f.p.Gw; w += 32) bm[w] = __ldcg(f.e.acc + q * f.p.Gw + w);
+            __syncwarp();
+            skip = mask_dead(bm, f.p.Gw, f.e.B, f.e.R, lane);
+            __syncwarp();
+            if (!skip && lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(k1 - k0));
+        }
+        if (!skip) {
+            const Slice<SW> s = fused_probe_range<SW, LPG, ETA>(f.p, start, k0, k1, lane, word0);
+            if (sub == 0) flush_slice<SW>(const_cast<uint32_t *>(f.e.acc), q, f.p.Gw, word0, s);
+        }
         __threadfence();
         __syncwarp();
         uint32_t last = 0;
@@ -831,7 +868,23 @@ __global__ void __launch_bounds__(FUSED_THREADS) k_fused(FusedArgs f) {
         const uint32_t q = f.short_list[s];
         uint64_t start;
         const uint64_t nk = fused_kmers(f, q, &start);
-        const Slice<SW> sl = fused_probe_range<SW, LPG, ETA>(f.p, start, 0, nk, lane, word0);
+        Slice<SW> sl;
+        slice_ones(sl);
+        const uint64_t seg = f.early_exit ? f.segment : (nk ? nk : 1);
+        for (uint64_t k0 = 0; k0 < nk; k0 += seg) {
+            const uint64_t k1 = k0 + seg < nk ? k0 + seg : nk;
+            slice_and(sl, fused_probe_range<SW, LPG, ETA>(f.p, start, k0, k1, lane, word0));
+            if (!f.early_exit) continue;
+            if (lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(k1 - k0));
+            if (k1 >= nk) break;
+            if (sub == 0)
+#pragma unroll
+                for (int w = 0; w < SW; ++w) bm[word0 + w] = sl.w[w];
+            __syncwarp();
+            const bool dead = mask_dead(bm, f.p.Gw, f.e.B, f.e.R, lane);
+            __syncwarp();
+            if (dead) break;
+        }
         if (sub == 0)
 #pragma unroll
             for (int w = 0; w < SW; ++w) bm[word0 + w] = sl.w[w];
@@ -1020,6 +1073,9 @@ cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry
     f.short_max = qs.short_max;
     f.user_bases = qs.user_bases;
     f.e = e;
+    f.early_exit = qs.early_exit;
+    f.segment = qs.segment;
+    f.probed = qs.probed;
     cudaError_t err = cudaMemsetAsync(qs.counters, 0, 4 * sizeof(uint32_t), s);
     if (err != cudaSuccess) return err;
     if (p.n == 0) return cudaSuccess;

@@ -80,6 +80,7 @@ def load():
             "rambo_query_seqs_noalloc": (i, [p, u64, p, u64, p, p, p]),
             "rambo_query_ranges_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
             "rambo_fold": (i, [p]),
+            "rambo_probed_kmers": (i, [p, C.POINTER(u64), i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -150,7 +151,7 @@ STAGES = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
 TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_per_sm",
                  "use_byte_table", "byte_table_max_mb", "query_path", "fused_tile_kmers",
                  "fused_short_max", "smem_docbits", "use_nibble_table",
-                 "expand_filter")
+                 "expand_filter", "early_exit", "early_exit_segment")
 
 
 class _Tuning(C.Structure):
@@ -336,6 +337,12 @@ class Index:
         cur.update(kw)
         t = _Tuning(**{f: int(cur[f]) for f in TUNING_FIELDS})
         _check(load().rambo_set_tuning(self._h, C.addressof(t)), "rambo_set_tuning")
+
+    def probed_kmers(self, reset: bool = False) -> int:
+        v = C.c_uint64(0)
+        _check(load().rambo_probed_kmers(self._h, C.byref(v), 1 if reset else 0),
+               "rambo_probed_kmers")
+        return v.value
 
     # ---------------------------------------------------------- profiling
     def profile_reset(self, timed_stages=()):

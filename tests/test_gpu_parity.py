@@ -321,3 +321,22 @@ def test_expansion_variants_on_many_kmer_queries(rambo_lib):
         got = idx.query_kmers_dev(_dev(kmers, np.int64))
         idx.sync()
         assert np.array_equal(rambo_lib.as_u32(got), want), st
+
+
+def test_early_exit_gives_identical_answers_and_probes_fewer_kmers(rambo_lib):
+    p = synth.Params(K=200, B=20, R=3, m=1 << 14, eta=2, k=31, seed=21)
+    rng = np.random.default_rng(17)
+    corpus = synth.family_corpus(rng, p, n_seeds=20, doc_len=3000, sub_rate=0.01)
+    # long random queries die after a few k-mers; document substrings do not
+    q = synth.sample_queries(rng, corpus, rng.integers(100, 2500, size=300), 0.5)
+    o = oracle_index(p, corpus)
+    want = o.query_seqs(q.packed, q.offsets)
+    idx = gpu_index(rambo_lib, p, corpus)
+    idx.set_tuning(query_path=1, fused_tile_kmers=256, fused_short_max=512, early_exit=0)
+    assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want)
+    idx.set_tuning(early_exit=1, early_exit_segment=128)
+    idx.probed_kmers(reset=True)
+    got = gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets)
+    probed = idx.probed_kmers(reset=True)
+    assert np.array_equal(got, want)
+    assert 0 < probed < q.n_kmers(p.k)
