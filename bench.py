@@ -36,7 +36,8 @@ METRIC = "k-mer queries/s and query bp/s on 1 GB300 (bit-exact vs oracle); servi
 UNIT = "k-mer queries/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-PROBE_SRC = os.path.join(ROOT, "paper_1910_04358_gb300", "csrc", "rambo_kernels_query.cu")
+CSRC = os.path.join(ROOT, "paper_1910_04358_gb300", "csrc")
+KERNEL_SRC = {"k_fused": "rambo_kernels_fused.cu", "k_probe_seqs": "rambo_kernels_probe.cu"}
 SECTOR = 32
 STAGES_ALL = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
 
@@ -169,17 +170,26 @@ def source_digest(path: str) -> str:
 
 
 def measured_traffic(workload: str, kernel: str):
-    """dram bytes per launch from a committed ncu capture, if the kernel source
-    has not changed since the counters were taken."""
+    """dram bytes per launch from a committed ncu capture, if the kernel's
+    source (and the shared device header) has not changed since the counters
+    were taken."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
         e = t[workload][kernel]
-        if e.get("source_sha") != source_digest(PROBE_SRC):
+        if e.get("source_sha") != kernel_digest(kernel):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
         return None
+
+
+def kernel_digest(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in (KERNEL_SRC[kernel], "rambo_query_common.cuh", "rambo_internal.cuh"):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------------------
@@ -328,6 +338,74 @@ def run_reference(args):
 # GPU arm
 
 
+def run_stream(args):
+    """Streaming update + query: epochs of document inserts, each followed by a
+    query batch over everything inserted so far.  A step is one epoch's query
+    batch; inserts are timed separately."""
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_1910_04358_gb300 import rambo, synth
+    wl = synth.stream_workload()
+    p = wl.params
+    idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=local)
+    info = idx.info
+    to_dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
+    n_epochs = min(wl.n_epochs, args.warmup + args.steps)
+    stream = torch.cuda.current_stream()
+    q_ms, q_kmers, q_bp, ins_ms, ins_kmers, timed = 0.0, 0, 0, 0.0, 0, 0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.time()
+    for e in range(n_epochs):
+        (ids, packed, offs), q = wl.epoch(e)
+        d_ids, d_p, d_o = to_dev(ids, np.int32), to_dev(packed, np.uint8), to_dev(offs, np.int64)
+        d_qp, d_qo = to_dev(q.packed, np.uint8), to_dev(q.offsets, np.int64)
+        out = torch.empty((q.n, idx.W), dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        idx.insert_batch_dev(d_ids, d_p, d_o)
+        ev[1].record(stream)
+        idx.query_seqs_dev(d_qp, d_qo, out=out)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if e >= args.warmup:
+            ins_ms += ev[0].elapsed_time(ev[1])
+            q_ms += ev[1].elapsed_time(ev[2])
+            ins_kmers += int(np.maximum(np.diff(offs.astype(np.int64)) - p.k + 1, 0).sum())
+            q_kmers += q.n_kmers(p.k)
+            q_bp += q.n_bases
+            timed += 1
+    idx.sync()
+    t_wall1 = time.time()
+    clocks.stop()
+    ms_step = q_ms / max(timed, 1)
+    peak, peak_src = measured_peak_gbs()
+    kpb = probe_bytes_per_kmer(info)
+    line = {
+        "metric": METRIC, "value": q_kmers / (q_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": timed, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+        "config": {"workload": "stream", "desc": "100,000 docs x 50 kbp from 2,000 seeds at 1%; "
+                   "R=6 B=316 m=2^28 eta=2 k=31 (64 GiB index); epochs of 1,000 docs, each "
+                   "followed by 10^4 queries of U[31,2000] bp (70% from inserted docs)",
+                   "l2": "inputs larger than L2: index %.1f GB" % (info["index_bytes"] / 1e9)},
+        "query_bp_per_s": q_bp / (q_ms / 1e3),
+        "insert": {"kmers_per_s": ins_kmers / (ins_ms / 1e3), "ms_per_epoch": ins_ms / max(timed, 1)},
+        "roofline": {"bound": "hbm", "kernel": "query step (all query kernels)",
+                     "achieved": q_kmers * kpb / (q_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": q_kmers * kpb / (q_ms / 1e3) / 1e9 / peak, "traffic": None,
+                     "bytes_per_kmer": kpb, "peak_source": peak_src},
+        "clocks": clocks.summary(t_wall0, t_wall1), "tuning": idx.get_tuning(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     rank, local, world = dist_setup("nccl")
@@ -386,7 +464,7 @@ def run_ours(args):
             tuning_source = f"cached ({os.path.relpath(autotune.CACHE_FILE, ROOT)})"
         else:
             outs = lambda: [t for t in (out_k, out_s) if t is not None]
-            tuned = autotune.autotune(idx, step, outs, reps=3)
+            tuned = autotune.autotune(idx, step, outs, reps=7)
             log(f"[autotune] best {tuned['best']} {tuned['ms']:.4f} ms/step")
             autotune.store_cached(autotune.CACHE_FILE, key, tuned["best"])
             tuning_source = "autotuned in this run"
@@ -470,7 +548,7 @@ def run_ours(args):
         alg_bytes += q.n * idx.W * 4
     peak, peak_src = measured_peak_gbs()
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-    traffic = measured_traffic(args.workload, dom)
+    traffic = measured_traffic(args.workload, "k_fused" if fused else "k_probe_seqs")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_fused_prep+k_fused" if fused else "k_probe_seqs",
@@ -492,18 +570,21 @@ def run_ours(args):
             if kmers.size else kmers
         pin_p = torch.from_numpy(q.packed).pin_memory().numpy()
         pin_o = torch.from_numpy(q.offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        pin_ok = torch.empty((kmers.size, idx.W), dtype=torch.int32).pin_memory().numpy() \
+            if kmers.size else None
+        pin_os = torch.empty((q.n, idx.W), dtype=torch.int32).pin_memory().numpy()
         e2e_steps = max(3, min(args.steps, 30))
         for _ in range(2):
             if kmers.size:
-                idx.query_kmers(pin_k)
-            idx.query_seqs(pin_p, pin_o)
+                idx.query_kmers(pin_k, out=pin_ok)
+            idx.query_seqs(pin_p, pin_o, out=pin_os)
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             if kmers.size:
-                idx.query_kmers(pin_k)
-            idx.query_seqs(pin_p, pin_o)
+                idx.query_kmers(pin_k, out=pin_ok)
+            idx.query_seqs(pin_p, pin_o, out=pin_os)
         t_e2e = (time.perf_counter() - t0) / e2e_steps
         t_e2e = max_over_ranks(t_e2e, world, dev)
         h2d = int(kmers.nbytes) + int(q.packed.nbytes) + int(q.offsets.nbytes)
@@ -567,7 +648,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["medium", "large", "tiny"], default="medium")
+    ap.add_argument("--workload", choices=["medium", "large", "tiny", "stream"], default="medium")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -582,6 +663,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "stream":
+        return run_stream(args)
     return run_ours(args)
 
 

@@ -193,9 +193,43 @@ int rambo_query_ranges_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64
                            const uint64_t *begins, const uint64_t *ends, uint32_t *out,
                            void *workspace, size_t workspace_bytes, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Documents of words (Section 5.4 "Document indexing": a document is a    */
+/* set of word unigrams).  A term is an arbitrary byte string; probe j of a */
+/* term is MurmurHash3_x64_128(term bytes, (uint32)(seed + j)) first word   */
+/* mod m, so index, partition and expansion are the k-mer ones.  Device     */
+/* buffers, asynchronous on `stream`.  Term t is bytes [term_offs[t],       */
+/* term_offs[t+1]) of `bytes` (bytes_len readable bytes); item i is terms   */
+/* [item_terms[i], item_terms[i+1]) (n+1 entries), and term_offs must have  */
+/* item_terms[n]+1 entries.  Terms past bytes_len are skipped and latched   */
+/* (rambo_sync).                                                            */
+
+/* Algorithm 1 for word documents: document i (id doc_ids[i]) is the terms
+ * [doc_terms[i], doc_terms[i+1]).  Needs no workspace. */
+int rambo_insert_words_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                           const uint8_t *bytes, uint64_t bytes_len, const uint64_t *term_offs,
+                           const uint64_t *doc_terms, void *stream);
+
+size_t rambo_query_words_workspace(const rambo_t *h, uint64_t n);
+
+/* Algorithm 2 for n word queries: query i passes a BFU iff every one of its
+ * terms [query_terms[i], query_terms[i+1]) does.  out receives n*W words. */
+int rambo_query_words_dev(rambo_t *h, uint64_t n, const uint8_t *bytes, uint64_t bytes_len,
+                          const uint64_t *term_offs, const uint64_t *query_terms, uint32_t *out,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
 /* Waits for `stream` and returns the first device-side error latched since
  * the last rambo_sync (then clears it), or RAMBO_OK. */
 int rambo_sync(rambo_t *h, void *stream);
+
+/* Replaces the partition functions by an explicit map: phi[d*R + r] (host,
+ * K*R values < B) is document d's bucket in repetition r.  This is how a
+ * stacked, document-sharded deployment is expressed as one index (Section
+ * 5.3: bucket b*tau(D) + phi_i(D) over S shards of b buckets each).  Allowed
+ * only before the first insert (RAMBO_ESTATE afterwards); RAMBO_EINVAL if a
+ * bucket is out of range.  Folding afterwards recomputes the default
+ * partition. */
+int rambo_set_partition(rambo_t *h, const uint32_t *phi);
 
 /* ---------------------------------------------------------------------- */
 /* Folding over (Section 5.3, Fig. 5): every repetition's BFUs of buckets   */

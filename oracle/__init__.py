@@ -81,6 +81,10 @@ def _load():
             "orc_is_inserted": (C.c_int, [p, u32]),
             "orc_num_filters_bits": (u64, [p]),
             "orc_fold": (C.c_int, [p]),
+            "orc_set_partition": (C.c_int, [p, p]),
+            "orc_word_position": (u64, [p, p, u64, u32]),
+            "orc_insert_words": (C.c_int, [p, u32, p, p, u64]),
+            "orc_query_words": (C.c_int, [p, p, p, u64, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -119,6 +123,13 @@ def unpack(packed: np.ndarray, begin: int, n: int) -> np.ndarray:
     out = np.zeros(max(n, 1), dtype=np.uint8)
     _load().orc_unpack(_ptr(packed), begin, n, _ptr(out))
     return out[:n]
+
+
+def _pack_words(words):
+    buf = np.frombuffer(b"".join(words) + b"\0", dtype=np.uint8)
+    offs = np.zeros(len(words) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(w) for w in words]) if words else []
+    return buf, offs
 
 
 class OracleError(RuntimeError):
@@ -205,6 +216,30 @@ class Rambo:
             _check(_load().orc_query_kmers(self._h, km.size, _ptr(km), _ptr(out), threads),
                    "query_kmers")
         return out
+
+    # -- documents of words (Section 5.4) ------------------------------------
+    def insert_words(self, doc_id: int, words: list[bytes]):
+        buf, offs = _pack_words(words)
+        _check(_load().orc_insert_words(self._h, doc_id, _ptr(buf), _ptr(offs), len(words)),
+               "insert_words")
+
+    def query_words(self, words: list[bytes]) -> np.ndarray:
+        buf, offs = _pack_words(words)
+        out = np.zeros(self.W, dtype=np.uint32)
+        _check(_load().orc_query_words(self._h, _ptr(buf), _ptr(offs), len(words), _ptr(out)),
+               "query_words")
+        return out
+
+    def word_position(self, word: bytes, j: int) -> int:
+        buf, _ = _pack_words([word])
+        return int(_load().orc_word_position(self._h, _ptr(buf), len(word), j))
+
+    # -- explicit partition (Section 5.3 routing) ------------------------------
+    def set_partition(self, phi):
+        """phi[d, r] = bucket of document d in repetition r; before any insert."""
+        a = np.ascontiguousarray(phi, dtype=np.uint32)
+        assert a.shape == (self.K, self.R)
+        _check(_load().orc_set_partition(self._h, _ptr(a)), "set_partition")
 
     # -- folding over (Section 5.3) -------------------------------------------
     def fold(self):

@@ -395,23 +395,14 @@ int orc_insert_batch(orc_rambo *o, uint32_t n, const uint32_t *ids, const uint8_
     return ORC_OK;
 }
 
-/* Algorithm 2 for a term set Q given as canonical codes.  Writes the K-bit
- * answer as ceil(K/32) uint32 words: document d is word d>>5, bit d&31. */
-static int orc_query_terms(const orc_rambo *o, const uint64_t *Q, uint64_t nq, uint32_t *out) {
+/* Algorithm 2 given the eta probe slots of every term of Q (pos[i*eta + j]).
+ * Writes the K-bit answer as ceil(K/32) uint32 words: document d is word
+ * d>>5, bit d&31. */
+static int orc_query_slots(const orc_rambo *o, const uint64_t *pos, uint64_t nq, uint32_t *out) {
     uint32_t W = (o->K + 31) / 32;
     uint8_t *G = (uint8_t *)calloc(o->K, 1);   /* G_r for the current r */
     uint8_t *A = (uint8_t *)malloc(o->K);      /* running intersection  */
-    uint64_t *pos = (uint64_t *)malloc(sizeof(uint64_t) * (nq ? nq : 1) * o->eta);
-    if (!G || !A || !pos) { free(G); free(A); free(pos); return ORC_ENOMEM; }
-    int rc = ORC_OK;
-    /* the eta probe positions of every term, one slot per (term, j) */
-    for (uint64_t i = 0; i < nq; ++i)
-        for (uint32_t j = 0; j < o->eta; ++j) {
-            int64_t s = orc_slot(o, orc_probe_position(o, Q[i], j));
-            if (s < 0) rc = ORC_EUNTRACKED;
-            pos[i * o->eta + j] = (uint64_t)s;
-        }
-    if (rc) { free(G); free(A); free(pos); return rc; }
+    if (!G || !A) { free(G); free(A); return ORC_ENOMEM; }
     memset(A, 1, o->K);
     for (uint32_t r = 0; r < o->R; ++r) {
         memset(G, 0, o->K);
@@ -430,8 +421,75 @@ static int orc_query_terms(const orc_rambo *o, const uint64_t *Q, uint64_t nq, u
     memset(out, 0, sizeof(uint32_t) * W);
     for (uint32_t d = 0; d < o->K; ++d)
         if (A[d]) out[d >> 5] |= (uint32_t)1 << (d & 31);
-    free(G); free(A); free(pos);
+    free(G); free(A);
     return ORC_OK;
+}
+
+/* Algorithm 2 for a term set Q given as canonical k-mer codes. */
+static int orc_query_terms(const orc_rambo *o, const uint64_t *Q, uint64_t nq, uint32_t *out) {
+    uint64_t *pos = (uint64_t *)malloc(sizeof(uint64_t) * (nq ? nq : 1) * o->eta);
+    if (!pos) return ORC_ENOMEM;
+    int rc = ORC_OK;
+    /* the eta probe positions of every term, one slot per (term, j) */
+    for (uint64_t i = 0; i < nq; ++i)
+        for (uint32_t j = 0; j < o->eta; ++j) {
+            int64_t s = orc_slot(o, orc_probe_position(o, Q[i], j));
+            if (s < 0) rc = ORC_EUNTRACKED;
+            pos[i * o->eta + j] = (uint64_t)s;
+        }
+    if (!rc) rc = orc_query_slots(o, pos, nq, out);
+    free(pos);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Documents of words (Section 5.4: each document is a set of word       */
+/* unigrams).  A term is an arbitrary byte string; probe j of a term is   */
+/* the first word of MurmurHash3_x64_128(term bytes, seed + j) mod m.     */
+
+uint64_t orc_word_position(const orc_rambo *o, const uint8_t *bytes, uint64_t len, uint32_t j) {
+    uint64_t h[2];
+    orc_mmh3_x64_128(bytes, len, (uint32_t)(o->seed + j), h);
+    return h[0] % o->m;
+}
+
+/* Algorithm 1 for document d given as n_terms byte strings: term t is bytes
+ * [term_offs[t], term_offs[t+1]). */
+int orc_insert_words(orc_rambo *o, uint32_t d, const uint8_t *bytes, const uint64_t *term_offs,
+                     uint64_t n_terms) {
+    if (d >= o->K) return ORC_ERANGE;
+    int rc = orc_register_doc(o, d);
+    if (rc) return rc;
+    for (uint64_t t = 0; t < n_terms; ++t) {
+        const uint8_t *w = bytes + term_offs[t];
+        const uint64_t len = term_offs[t + 1] - term_offs[t];
+        for (uint32_t r = 0; r < o->R; ++r) {
+            uint64_t f = (uint64_t)r * o->B + o->bucket[(uint64_t)d * o->R + r];
+            for (uint32_t j = 0; j < o->eta; ++j) {
+                int64_t slot = orc_slot(o, orc_word_position(o, w, len, j));
+                if (slot >= 0) orc_set_bit(o->filter[f], (uint64_t)slot, 0);
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* Algorithm 2 for a query given as a set of words (every word must pass). */
+int orc_query_words(const orc_rambo *o, const uint8_t *bytes, const uint64_t *term_offs,
+                    uint64_t n_terms, uint32_t *out) {
+    uint64_t *pos = (uint64_t *)malloc(sizeof(uint64_t) * (n_terms ? n_terms : 1) * o->eta);
+    if (!pos) return ORC_ENOMEM;
+    int rc = ORC_OK;
+    for (uint64_t t = 0; t < n_terms; ++t)
+        for (uint32_t j = 0; j < o->eta; ++j) {
+            int64_t s = orc_slot(o, orc_word_position(o, bytes + term_offs[t],
+                                                      term_offs[t + 1] - term_offs[t], j));
+            if (s < 0) rc = ORC_EUNTRACKED;
+            pos[t * o->eta + j] = (uint64_t)s;
+        }
+    if (!rc) rc = orc_query_slots(o, pos, n_terms, out);
+    free(pos);
+    return rc;
 }
 
 /* Terms(q) for the sequence of n_bases bases starting at base `begin`. */
@@ -508,6 +566,17 @@ int orc_query_seqs(const orc_rambo *o, uint64_t n, const uint8_t *packed, const 
 int orc_query_kmers(const orc_rambo *o, uint64_t n, const uint64_t *kmers, uint32_t *out,
                     uint32_t n_threads) {
     return orc_query_many(o, n, NULL, NULL, kmers, out, n_threads);
+}
+
+/* Explicit partition (Section 5.3 two-level routing: a stacked RAMBO uses
+ * bucket b*tau(D) + phi(D)).  phi[d*R + r] < B; only before any insert. */
+int orc_set_partition(orc_rambo *o, const uint32_t *phi) {
+    for (uint32_t d = 0; d < o->K; ++d)
+        if (o->inserted[d]) return ORC_EINVAL;
+    for (uint64_t i = 0; i < (uint64_t)o->K * o->R; ++i)
+        if (phi[i] >= o->B) return ORC_EINVAL;
+    memcpy(o->bucket, phi, sizeof(uint32_t) * (uint64_t)o->K * o->R);
+    return ORC_OK;
 }
 
 /* Folding over (Section 5.3, Fig. 5): the BFUs of the second half of every

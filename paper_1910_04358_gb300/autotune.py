@@ -20,15 +20,17 @@ CACHE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_ca
 
 KNOBS = (
     ("query_path", (0, 1)),
+    # expansion variant before its grid: a variant's best grid differs; the
+    # filter takes precedence over the nibble table, so it is decided first
+    ("expand_filter", (0, 1)),
+    ("use_nibble_table", (0, 1)),
+    ("use_byte_table", (0, 1)),
+    ("smem_docbits", (0, 1)),
+    ("expand_ctas_per_sm", (2, 4, 8, 16, 32)),
     ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
     ("fused_tile_kmers", (256, 512, 1024, 2048, 4096)),
     ("fused_short_max", (64, 256, 1024, 4096)),
     ("probe_min_kmers_per_warp", (0, 256, 1024, 4096)),
-    ("expand_ctas_per_sm", (2, 4, 8, 16, 32)),
-    ("use_byte_table", (0, 1)),
-    ("smem_docbits", (0, 1)),
-    ("use_nibble_table", (0, 1)),
-    ("expand_filter", (0, 1)),
 )
 
 
@@ -49,7 +51,7 @@ def _time(run, reps: int):
     return best
 
 
-def autotune(idx, run, outputs, reps: int = 5, knobs=KNOBS, verbose: bool = False) -> dict:
+def autotune(idx, run, outputs, reps: int = 7, knobs=KNOBS, verbose: bool = False) -> dict:
     """Tunes `idx` for the batch that `run()` enqueues on the current stream.
 
     `outputs()` returns the tensors holding the batch's answers after a run;

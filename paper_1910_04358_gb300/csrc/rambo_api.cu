@@ -22,6 +22,7 @@ struct rambo {
     unsigned long long *d_probed;  // k-mers probed under early exit
     void *d_stage;           // host-call staging + workspace
     size_t stage_bytes;
+    bool any_inserted;       // set by the first insert call
     uint32_t *d_tab;         // byte table for the expansion (or null)
     uint32_t *d_ntab;        // nibble table for the expansion (or null)
     rambo_tuning_t tune;
@@ -154,7 +155,7 @@ int probe_grid(const rambo_t *h) {
 int apply_bytetab(rambo_t *h) {
     const Geometry &g = h->g;
     const uint64_t nbytes = nibtab_words(g.B, g.R, g.W) * 4;
-    if (nbytes <= 96 * 1024 && g.Gw <= 32 && g.W <= 64) {
+    if (nbytes <= 96 * 1024 && g.W <= 128) {
         if (!h->d_ntab) RAMBO_TRY(cudaMalloc(&h->d_ntab, nbytes));
         RAMBO_TRY(launch_build_nibtab(h->d_docbits, g.B, g.R, g.W, h->d_ntab, h->sm_count, h->stream));
     } else if (h->d_ntab) {
@@ -320,7 +321,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
                      h->tune.expand_filter};
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
-        RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
+        RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
     }
     return RAMBO_OK;
 }
@@ -352,7 +353,7 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
                      h->tune.expand_filter};
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
-        RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, s));
+        RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
     }
     return RAMBO_OK;
 }
@@ -360,6 +361,7 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
 int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_t *packed,
                    uint64_t packed_bytes, const uint64_t *offsets, void *ws, cudaStream_t s) {
     const Geometry &g = h->g;
+    h->any_inserted = true;
     const InsWs L = ins_ws(n);
     char *w = static_cast<char *>(ws);
     uint64_t *kcum = reinterpret_cast<uint64_t *>(w + L.kcum);
@@ -523,7 +525,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.query_path = 0;
     h->tune.smem_docbits = 1;
     h->tune.use_nibble_table = 1;
-    h->tune.expand_filter = 1;
+    h->tune.expand_filter = 0;
     h->tune.early_exit = 0;
     h->tune.early_exit_segment = 256;
     h->tune.fused_tile_kmers = 1024;
@@ -717,6 +719,107 @@ int rambo_query_seqs(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64
     RAMBO_TRY(cudaMemcpyAsync(out, d_out, n * (uint64_t)h->g.W * 4, cudaMemcpyDeviceToHost, h->stream));
     RAMBO_TRY(cudaStreamSynchronize(h->stream));
     return read_and_clear_err(h);
+}
+
+// ---------------------------------------------------- documents of words
+
+int rambo_insert_words_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                           const uint8_t *bytes, uint64_t bytes_len, const uint64_t *term_offs,
+                           const uint64_t *doc_terms, void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n_docs == 0) return RAMBO_OK;
+    if (!doc_ids || !term_offs || !doc_terms || (!bytes && bytes_len)) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Geometry &g = h->g;
+    h->any_inserted = true;
+    {
+        StageScope sc(h, RAMBO_STAGE_REGISTER, s, 1);
+        RAMBO_TRY(launch_register_docs(doc_ids, n_docs, h->d_phi, g.K, g.R, g.B, g.W, h->d_docbits,
+                                       h->d_err, s));
+    }
+    WordArgs a{};
+    a.index = h->d_index;
+    a.m = g.m;
+    a.m_pow2 = (g.m & (g.m - 1)) == 0;
+    a.Gw = g.Gw; a.B = g.B; a.R = g.R; a.K = g.K; a.eta = g.eta;
+    a.seed32 = (uint32_t)g.seed;
+    a.phi = h->d_phi;
+    a.doc_ids = doc_ids;
+    a.bytes = bytes;
+    a.bytes_len = bytes_len;
+    a.term_offs = term_offs;
+    a.item_terms = doc_terms;
+    a.n = n_docs;
+    a.err = h->d_err;
+    {
+        StageScope sc(h, RAMBO_STAGE_INSERT, s, 1);
+        RAMBO_TRY(launch_insert_words(a, h->sm_count, s));
+    }
+    if (h->d_tab) RAMBO_TRY(launch_build_bytetab(h->d_docbits, g.B, g.R, g.W, h->d_tab, h->sm_count, s));
+    if (h->d_ntab) RAMBO_TRY(launch_build_nibtab(h->d_docbits, g.B, g.R, g.W, h->d_ntab, h->sm_count, s));
+    return RAMBO_OK;
+}
+
+size_t rambo_query_words_workspace(const rambo_t *h, uint64_t n) {
+    return h ? align_up(n * (uint64_t)h->g.Gw * 4) : 0;
+}
+
+int rambo_query_words_dev(rambo_t *h, uint64_t n, const uint8_t *bytes, uint64_t bytes_len,
+                          const uint64_t *term_offs, const uint64_t *query_terms, uint32_t *out,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n == 0) return RAMBO_OK;
+    if (!term_offs || !query_terms || !out || !workspace || (!bytes && bytes_len) ||
+        workspace_bytes < align_up(n * (uint64_t)h->g.Gw * 4) ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Geometry &g = h->g;
+    uint32_t *acc = static_cast<uint32_t *>(workspace);
+    RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
+    WordArgs a{};
+    a.index_ro = h->d_index;
+    a.m = g.m;
+    a.m_pow2 = (g.m & (g.m - 1)) == 0;
+    a.Gw = g.Gw; a.B = g.B; a.R = g.R; a.K = g.K; a.eta = g.eta;
+    a.seed32 = (uint32_t)g.seed;
+    a.bytes = bytes;
+    a.bytes_len = bytes_len;
+    a.term_offs = term_offs;
+    a.item_terms = query_terms;
+    a.n = n;
+    a.acc = acc;
+    a.err = h->d_err;
+    {
+        StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 1);
+        RAMBO_TRY(launch_probe_words(a, h->sm_count, s));
+    }
+    ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
+                 h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K, h->tune.expand_filter};
+    {
+        StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
+        RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
+    }
+    return RAMBO_OK;
+}
+
+// -------------------------------------------------------- explicit partition
+
+int rambo_set_partition(rambo_t *h, const uint32_t *phi) {
+    if (!h || !phi) return RAMBO_EINVAL;
+    if (h->any_inserted) return RAMBO_ESTATE;
+    const uint64_t n = (uint64_t)h->g.K * h->g.R;
+    for (uint64_t i = 0; i < n; ++i)
+        if (phi[i] >= h->g.B) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    RAMBO_TRY(cudaMemcpy(h->d_phi, phi, n * 4, cudaMemcpyHostToDevice));
+    return RAMBO_OK;
 }
 
 // ---------------------------------------------------------------- folding

@@ -217,6 +217,28 @@ struct InsertArgs {
     uint32_t *err;
 };
 
+// Word documents (Section 5.4): term t is bytes [term_offs[t], term_offs[t+1])
+// of `bytes`; item i (a document or a query) is terms [item_terms[i],
+// item_terms[i+1]).
+struct WordArgs {
+    uint32_t *index;           // insert: written with atomicOr
+    const uint32_t *index_ro;  // probe: read only
+    uint64_t m;
+    uint32_t m_pow2;
+    uint32_t Gw, B, R, K, eta, seed32;
+    const uint32_t *phi;       // K x R
+    const uint32_t *doc_ids;   // insert: n
+    const uint8_t *bytes;
+    uint64_t bytes_len;
+    const uint64_t *term_offs;
+    const uint64_t *item_terms;  // n+1
+    uint64_t n;
+    uint32_t *acc;             // probe: n x Gw, preset to all ones
+    uint32_t *err;
+};
+cudaError_t launch_insert_words(const WordArgs &a, int sm_count, cudaStream_t s);
+cudaError_t launch_probe_words(const WordArgs &a, int sm_count, cudaStream_t s);
+
 // Launchers (rambo_kernels_*.cu).  All enqueue on `s` and return the launch
 // status.
 cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, uint64_t seed,
@@ -259,7 +281,7 @@ cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry
                          const FusedQueues &qs, int grid_override, int sm_count, cudaStream_t s);
 
 // max_blocks caps the expansion grid
-cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, cudaStream_t s);
+cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cudaStream_t s);
 uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W);
 uint64_t nibtab_words(uint32_t B, uint32_t R, uint32_t W);
 cudaError_t launch_build_nibtab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,

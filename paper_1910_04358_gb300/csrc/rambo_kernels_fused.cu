@@ -1,0 +1,304 @@
+// rambo_kernels_fused.cu -- the persistent fused query (probe and
+// expansion in one launch with length-bucketed work queues).
+#include "rambo_query_common.cuh"
+
+namespace rgpu {
+namespace {
+
+// ---------------------------------------------------------------------------
+// persistent fused query: length-bucketed work queues in one launch.
+//
+// Before the launch, a prefix scan numbers the tiles of the long queries
+// (more than short_max k-mers; ceil(k-mers / tile) tiles each) into one
+// global range, and a prep kernel (one thread per query) appends each short
+// query to the short queue and sets each long query's bucket mask to all
+// ones and its completion counter to zero.  The persistent kernel's warps
+// then
+//   1. claim long-query tiles with one atomicAdd on a global tile counter
+//      (tile -> query by binary search in the tile prefix); a tile's AND is
+//      flushed with atomicAnd, and the warp that completes a query's last
+//      tile expands its answer;
+//   2. then take whole short queries from the short queue: the warp probes
+//      all k-mers, combines the lanes' slices into the bucket mask in shared
+//      memory and expands the answer itself, with no global round trip.
+// No warp ever waits on another.  Every k-mer of every query is probed; the
+// answers are the plain path's.
+constexpr int FUSED_THREADS = 256;
+
+struct FusedArgs {
+    ProbeArgs p;                 // index, geometry, batch (kcum unused)
+    uint32_t *counters;          // [0] short count [1] short head [2..3] 64-bit tile head
+    uint32_t *short_list;        // n
+    const uint64_t *tile_prefix; // n+1
+    uint32_t *done;              // n (long queries)
+    uint32_t tile;               // k-mers per long tile
+    uint32_t short_max;          // k-mers of the longest short query
+    uint64_t user_bases;         // bases addressable from the caller's pointer
+    ExpandArgs e;                // acc = bucket masks of long queries
+    uint32_t early_exit;         // 1: stop probing a query once a repetition row is empty
+    uint32_t segment;            // early exit: k-mers between checks of a short query
+    unsigned long long *probed;  // early exit: k-mers actually probed (or null)
+};
+
+// True when some repetition's row of the bucket mask bm (shared memory) has
+// no bit set: the answer is then empty whatever the remaining k-mers give.
+__device__ __forceinline__ bool mask_dead(const uint32_t *bm, uint32_t Gw, uint32_t B, uint32_t R,
+                                          int lane) {
+    bool dead = false;
+    for (uint32_t r0 = 0; r0 < R; r0 += 32) {
+        const uint32_t r = r0 + lane;
+        bool empty = false;
+        if (r < R) {
+            empty = true;
+            for (uint32_t i = 0; i < B && empty; i += 32) {
+                const uint32_t bit = r * B + i, wi = bit >> 5, sh = bit & 31;
+                uint32_t chunk = bm[wi];
+                if (sh) chunk = __funnelshift_r(chunk, wi + 1 < Gw ? bm[wi + 1] : 0u, sh);
+                const uint32_t nb = B - i < 32 ? B - i : 32;
+                if (nb < 32) chunk &= (1u << nb) - 1u;
+                if (chunk) empty = false;
+            }
+        }
+        if (__any_sync(FULL, empty)) dead = true;
+    }
+    return dead;
+}
+
+__device__ __forceinline__ uint64_t fused_kmers(const FusedArgs &f, uint64_t q, uint64_t *start) {
+    const uint64_t b0 = f.p.offsets[q], b1 = f.p.ends[q];
+    *start = b0;
+    if (b1 < b0 || b1 > f.user_bases) return 0;
+    const uint64_t L = b1 - b0;
+    return L >= f.p.k ? L - f.p.k + 1 : 0;
+}
+
+__global__ void k_fused_prep(FusedArgs f) {
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= f.p.n) return;
+    if (f.tile_prefix[q + 1] == f.tile_prefix[q]) {
+        f.short_list[atomicAdd(&f.counters[0], 1u)] = (uint32_t)q;
+    } else {
+        uint32_t *acc = const_cast<uint32_t *>(f.e.acc);  // the masks this launch owns
+        for (uint32_t w = 0; w < f.p.Gw; ++w) acc[q * f.p.Gw + w] = FULL;
+        f.done[q] = 0;
+    }
+}
+
+// AND of the groups of k-mers [k0, k1) of one query, per lane slice (every
+// lane of the warp works on the same query).
+template <int SW, int LPG, int ETA>
+__device__ __forceinline__ Slice<SW> fused_probe_range(const ProbeArgs &a, uint64_t start,
+                                                        uint64_t k0, uint64_t k1, int lane,
+                                                        uint32_t word0) {
+    constexpr int RIF = LPG == 1 ? 8 : 4;  // rounds whose loads are in flight together
+    constexpr int NT = LPG >= RIF ? 1 : RIF / LPG;
+    constexpr int KPR = 32 / LPG;
+    constexpr int ROUNDS = NT * LPG;
+    constexpr int STEP = 32 * NT;
+    const int sub = lane / LPG;
+    Slice<SW> accv;
+    slice_ones(accv);
+    for (uint32_t jb = 0; jb < a.eta; jb += ETA) {
+        for (uint64_t base = k0; base < k1; base += STEP) {
+            uint32_t pos[NT][ETA];
+            bool val[NT];
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const uint64_t g = base + (uint64_t)t * 32 + lane;
+                val[t] = g < k1;
+                uint64_t c = 0;
+                if (val[t])
+                    c = canonical_from_window(base_window(a.packed, a.packed_bytes, start + a.base_shift + g), a.k);
+                const uint64_t km = mh_mix_key(c);
+#pragma unroll
+                for (int e = 0; e < ETA; ++e) {
+                    const uint32_t j = jb + e < a.eta ? jb + e : a.eta - 1;
+                    pos[t][e] = reduce_pos(mh_first_word(km, a.seed32 + j), a.m, a.m_pow2);
+                }
+            }
+#pragma unroll
+            for (int rg = 0; rg < ROUNDS; rg += RIF) {
+                Slice<SW> v[RIF][ETA];
+#pragma unroll
+                for (int rr = 0; rr < RIF; ++rr) {
+                    const int rho = rg + rr;
+                    const int t = rho / LPG;
+                    const int src = (rho % LPG) * KPR + sub;
+                    const bool vs = __shfl_sync(FULL, (int)val[t], src) != 0;
+#pragma unroll
+                    for (int e = 0; e < ETA; ++e) {
+                        const uint32_t p = __shfl_sync(FULL, pos[t][e], src);
+                        if (vs) v[rr][e] = ld_slice<SW>(a.index + (uint64_t)p * a.Gw + word0);
+                        else slice_ones(v[rr][e]);
+                    }
+                }
+#pragma unroll
+                for (int rr = 0; rr < RIF; ++rr)
+#pragma unroll
+                    for (int e = 0; e < ETA; ++e) slice_and(accv, v[rr][e]);
+            }
+        }
+    }
+    // combine the lanes that hold the same slice
+#pragma unroll
+    for (int w = 0; w < SW; ++w)
+#pragma unroll
+        for (int off = LPG; off < 32; off <<= 1) accv.w[w] &= __shfl_xor_sync(FULL, accv.w[w], off);
+    return accv;
+}
+
+template <int SW, int LPG, int ETA, int C>
+// three resident blocks per SM fit without spills for groups read by 4+
+// lanes; one-lane groups keep 16 loads per lane in flight at two
+__global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(FusedArgs f) {
+    __shared__ uint32_t bm_smem[FUSED_THREADS / 32][128];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *bm = bm_smem[wib];
+    const int sub = lane / LPG;
+    const uint32_t word0 = (lane % LPG) * SW;
+    const uint32_t n_short = f.counters[0];
+    const uint64_t n_tiles = f.tile_prefix[f.p.n];
+    const uint32_t chunks = (f.e.W + 32 * C - 1) / (32 * C);
+
+    // 1. long queries, tile by tile
+    while (true) {
+        uint64_t t = 0;
+        if (lane == 0) t = atomicAdd(reinterpret_cast<unsigned long long *>(f.counters + 2), 1ULL);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= n_tiles) break;
+        // the query whose tile range holds t: largest q with tile_prefix[q] <= t
+        uint64_t lo = 0, hi = f.p.n;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (f.tile_prefix[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const uint64_t q = lo;
+        const uint64_t tiles = f.tile_prefix[q + 1] - f.tile_prefix[q];
+        uint64_t start;
+        const uint64_t nk = fused_kmers(f, q, &start);
+        const uint64_t k0 = (t - f.tile_prefix[q]) * f.tile;
+        const uint64_t k1 = k0 + f.tile < nk ? k0 + f.tile : nk;
+        bool skip = false;
+        if (f.early_exit) {  // a tile of an already-empty query changes nothing
+            for (uint32_t w = lane; w < f.p.Gw; w += 32) bm[w] = __ldcg(f.e.acc + q * f.p.Gw + w);
+            __syncwarp();
+            skip = mask_dead(bm, f.p.Gw, f.e.B, f.e.R, lane);
+            __syncwarp();
+            if (!skip && lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(k1 - k0));
+        }
+        if (!skip) {
+            const Slice<SW> s = fused_probe_range<SW, LPG, ETA>(f.p, start, k0, k1, lane, word0);
+            if (sub == 0) flush_slice<SW>(const_cast<uint32_t *>(f.e.acc), q, f.p.Gw, word0, s);
+        }
+        __threadfence();
+        __syncwarp();
+        uint32_t last = 0;
+        if (lane == 0) last = atomicAdd(&f.done[q], 1u) == tiles - 1;
+        last = __shfl_sync(FULL, last, 0);
+        if (last) {
+            __threadfence();
+            for (uint32_t w = lane; w < f.p.Gw; w += 32) bm[w] = __ldcg(f.e.acc + q * f.p.Gw + w);
+            __syncwarp();
+            for (uint32_t c = 0; c < chunks; ++c) expand_one<C>(f.e, bm, q, c * 32 * C + lane, lane);
+            __syncwarp();
+        }
+    }
+    // 2. short queries, one warp each, probe and expand fused
+    while (true) {
+        uint32_t s = 0;
+        if (lane == 0) s = atomicAdd(&f.counters[1], 1u);
+        s = __shfl_sync(FULL, s, 0);
+        if (s >= n_short) break;
+        const uint32_t q = f.short_list[s];
+        uint64_t start;
+        const uint64_t nk = fused_kmers(f, q, &start);
+        Slice<SW> sl;
+        slice_ones(sl);
+        const uint64_t seg = f.early_exit ? f.segment : (nk ? nk : 1);
+        for (uint64_t k0 = 0; k0 < nk; k0 += seg) {
+            const uint64_t k1 = k0 + seg < nk ? k0 + seg : nk;
+            slice_and(sl, fused_probe_range<SW, LPG, ETA>(f.p, start, k0, k1, lane, word0));
+            if (!f.early_exit) continue;
+            if (lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(k1 - k0));
+            if (k1 >= nk) break;
+            if (sub == 0)
+#pragma unroll
+                for (int w = 0; w < SW; ++w) bm[word0 + w] = sl.w[w];
+            __syncwarp();
+            const bool dead = mask_dead(bm, f.p.Gw, f.e.B, f.e.R, lane);
+            __syncwarp();
+            if (dead) break;
+        }
+        if (sub == 0)
+#pragma unroll
+            for (int w = 0; w < SW; ++w) bm[word0 + w] = sl.w[w];
+        __syncwarp();
+        for (uint32_t c = 0; c < chunks; ++c) expand_one<C>(f.e, bm, q, c * 32 * C + lane, lane);
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+template <int SW, int LPG, int ETA, int C>
+cudaError_t launch_fused_t(const FusedArgs &f, int grid_override, int sm_count, cudaStream_t s) {
+    static int occ = blocks_per_sm(k_fused<SW, LPG, ETA, C>, FUSED_THREADS, 0);
+    const int grid = grid_override > 0 ? grid_override : sm_count * occ;
+    k_fused<SW, LPG, ETA, C><<<grid, FUSED_THREADS, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+template <int SW, int LPG, int ETA>
+cudaError_t launch_fused_c(const FusedArgs &f, int go, int sm, cudaStream_t s) {
+    if (f.e.W > 64) return launch_fused_t<SW, LPG, ETA, 4>(f, go, sm, s);
+    return launch_fused_t<SW, LPG, ETA, 1>(f, go, sm, s);
+}
+
+template <int SW, int LPG>
+cudaError_t launch_fused_e(const FusedArgs &f, int go, int sm, cudaStream_t s) {
+    switch (f.p.eta) {
+        case 1: return launch_fused_c<SW, LPG, 1>(f, go, sm, s);
+        case 2: return launch_fused_c<SW, LPG, 2>(f, go, sm, s);
+        default: return launch_fused_c<SW, LPG, 4>(f, go, sm, s);
+    }
+}
+
+bool fused_supported(const Geometry &g) { return g.chunks == 1 && g.Gw <= 128; }
+
+cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry &g,
+                         const FusedQueues &qs, int grid_override, int sm_count, cudaStream_t s) {
+    if (!fused_supported(g)) return cudaErrorInvalidValue;
+    FusedArgs f{};
+    f.p = p;
+    f.counters = qs.counters;
+    f.short_list = qs.short_list;
+    f.tile_prefix = qs.tile_prefix;
+    f.done = qs.done;
+    f.tile = qs.tile;
+    f.short_max = qs.short_max;
+    f.user_bases = qs.user_bases;
+    f.e = e;
+    f.early_exit = qs.early_exit;
+    f.segment = qs.segment;
+    f.probed = qs.probed;
+    cudaError_t err = cudaMemsetAsync(qs.counters, 0, 4 * sizeof(uint32_t), s);
+    if (err != cudaSuccess) return err;
+    if (p.n == 0) return cudaSuccess;
+    k_fused_prep<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(f);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (g.SW == 1) return launch_fused_e<1, 1>(f, grid_override, sm_count, s);
+    if (g.SW == 2) return launch_fused_e<2, 1>(f, grid_override, sm_count, s);
+    switch (g.LPG) {
+        case 1: return launch_fused_e<4, 1>(f, grid_override, sm_count, s);
+        case 2: return launch_fused_e<4, 2>(f, grid_override, sm_count, s);
+        case 4: return launch_fused_e<4, 4>(f, grid_override, sm_count, s);
+        case 8: return launch_fused_e<4, 8>(f, grid_override, sm_count, s);
+        case 16: return launch_fused_e<4, 16>(f, grid_override, sm_count, s);
+        case 32: return launch_fused_e<4, 32>(f, grid_override, sm_count, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rgpu

@@ -1,0 +1,272 @@
+// rambo_query_common.cuh -- device helpers shared by the query kernels
+// (probe, expansion, persistent fused path); included by each of their
+// translation units, never by host-only code.
+#pragma once
+
+#include "rambo_internal.cuh"
+
+namespace rgpu {
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr uint32_t NONE = 0xffffffffu;
+constexpr int PROBE_THREADS = 256;
+
+__device__ __forceinline__ uint32_t reduce_pos(uint64_t h, uint64_t m, uint32_t m_pow2) {
+    return (uint32_t)(m_pow2 ? (h & (m - 1)) : (h % m));
+}
+
+// Largest q in [0, n) with kcum[q] <= g, given kcum[0] <= g < kcum[n].
+__device__ __forceinline__ uint64_t find_query(const uint64_t *kcum, uint64_t n, uint64_t g) {
+    uint64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (kcum[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int SW>
+__device__ __forceinline__ void slice_ones(Slice<SW> &s) {
+#pragma unroll
+    for (int w = 0; w < SW; ++w) s.w[w] = FULL;
+}
+
+template <int SW>
+__device__ __forceinline__ void slice_and(Slice<SW> &a, const Slice<SW> &b) {
+#pragma unroll
+    for (int w = 0; w < SW; ++w) a.w[w] &= b.w[w];
+}
+
+// atomicAnd of one lane's slice into a query's bucket mask (all-ones words
+// change nothing and are skipped).
+template <int SW>
+__device__ __forceinline__ void flush_slice(uint32_t *acc, uint64_t q, uint32_t Gw, uint32_t word0,
+                                            const Slice<SW> &v) {
+    uint32_t *p = acc + q * Gw + word0;
+#pragma unroll
+    for (int w = 0; w < SW; ++w)
+        if (v.w[w] != FULL) atomicAnd(p + w, v.w[w]);
+}
+
+// Per-warp contiguous range of the flattened k-mer index space [0, T).
+template <int STEP>
+__device__ __forceinline__ void warp_range(uint64_t T, uint32_t min_chunk, uint64_t &c0, uint64_t &c1) {
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    uint64_t per = (T + nwarps - 1) / nwarps;
+    if (per < min_chunk) per = min_chunk;
+    per = (per + STEP - 1) / STEP * STEP;
+    if (per < 2 * STEP) per = 2 * STEP;
+    c0 = warp * per;
+    c1 = c0 + per < T ? c0 + per : T;
+}
+
+// ---------------------------------------------------------------------------
+// expand.  Work unit = (query, chunk of 32*C output words); one warp per unit
+// (grid-stride), no block barriers.  For repetition r the bucket row is bits
+// [r*B, r*B+B) of the query's bucket mask, read as ceil(B/8) bytes.  The
+// union of the passing buckets' document bitmaps is built byte by byte:
+//  - with the byte table (the precomputed OR of DocBits over every 8-bucket
+//    pattern), every nonzero byte costs exactly one table row; the lanes
+//    first extract the bytes of 16/C (repetition, byte) pairs in parallel,
+//    then every lane issues all of those row loads before consuming any, so
+//    a query's loads are in flight together instead of one L2 round trip each;
+//  - without the table, each set bit costs one DocBits row.
+// The answer is the AND of the R unions; a repetition with no passing bucket,
+// or an all-zero running AND, ends the unit early.
+constexpr int EXPAND_THREADS = 256;
+constexpr size_t SMEM_DOCBITS_MAX = 96 * 1024;
+
+// Byte j of repetition r's bucket row (buckets 8j .. 8j+7), masked to B.
+// (bm may point to global or shared memory.)
+__device__ __forceinline__ uint32_t row_byte(const uint32_t *bm, uint32_t Gw, uint32_t B, uint32_t r,
+                                             uint32_t j) {
+    const uint32_t bit = r * B + 8 * j;
+    uint64_t two = bm[bit >> 5];
+    if ((bit & 31) > 24 && (bit >> 5) + 1 < Gw) two |= (uint64_t)bm[(bit >> 5) + 1] << 32;
+    const uint32_t nb = B - 8 * j < 8 ? B - 8 * j : 8;
+    return (uint32_t)(two >> (bit & 31)) & ((1u << nb) - 1u);
+}
+
+template <int C>
+__device__ __forceinline__ void expand_unit_table(const ExpandArgs &a, const uint32_t *bm, uint64_t q,
+                                                  uint32_t w0, int lane) {
+    constexpr int PB = 16 / C;  // (repetition, byte) pairs per batch
+    const uint32_t NJ = (a.B + 7) / 8;
+    const uint32_t NP = a.R * NJ;
+    uint32_t res[C], o[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        res[c] = FULL;
+        o[c] = 0;
+    }
+    bool row_any = false, dead = false;
+    uint32_t j0 = 0;  // byte index (within its repetition) of pair p0
+    for (uint32_t p0 = 0; p0 < NP && !dead; p0 += PB) {
+        uint32_t mine = 0;
+        if (lane < PB && p0 + lane < NP) {
+            const uint32_t p = p0 + lane;
+            const uint32_t r = p / NJ;
+            mine = row_byte(bm, a.Gw, a.B, r, p - r * NJ);
+        }
+        uint32_t v[PB];
+        uint32_t val[PB][C];
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            v[t] = __shfl_sync(FULL, mine, t);
+            const uint32_t p = p0 + t;
+            const uint32_t *row = a.tab + ((uint64_t)p * 256 + v[t]) * a.W;  // p = r*NJ + j
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const uint32_t w = w0 + 32 * c;
+                val[t][c] = (v[t] && w < a.W) ? __ldg(row + w) : 0u;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const uint32_t p = p0 + t;
+            if (p >= NP) break;
+#pragma unroll
+            for (int c = 0; c < C; ++c) o[c] |= val[t][c];
+            row_any |= v[t] != 0;
+            if (j0 == NJ - 1) {  // repetition complete
+                if (!row_any) dead = true;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    res[c] &= o[c];
+                    o[c] = 0;
+                }
+                row_any = false;
+                j0 = 0;
+            } else {
+                ++j0;
+            }
+        }
+        uint32_t nz = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) nz |= res[c];
+        if (!__any_sync(FULL, nz)) dead = true;
+    }
+    uint32_t *out = a.out + q * a.W;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const uint32_t w = w0 + 32 * c;
+        if (w < a.W) out[w] = dead ? 0u : res[c];
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void expand_unit_sparse(const ExpandArgs &a, const uint32_t *bm, uint64_t q,
+                                                   uint32_t w0) {
+    const uint32_t NJ = (a.B + 7) / 8;
+    uint32_t res[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) res[c] = FULL;
+    bool dead = false;
+    for (uint32_t r = 0; r < a.R && !dead; ++r) {
+        uint32_t o[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) o[c] = 0;
+        bool any = false;
+        for (uint32_t j = 0; j < NJ; ++j) {
+            uint32_t v = row_byte(bm, a.Gw, a.B, r, j);
+            any |= v != 0;
+            while (v) {
+                const uint32_t b = 8 * j + __ffs(v) - 1;
+                v &= v - 1;
+                const uint32_t *row = a.docbits + (uint64_t)(r * a.B + b) * a.W;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t w = w0 + 32 * c;
+                    if (w < a.W) o[c] |= __ldg(row + w);
+                }
+            }
+        }
+        uint32_t nz = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            res[c] &= o[c];
+            nz |= res[c];
+        }
+        if (!any || !__any_sync(FULL, nz)) dead = true;
+    }
+    uint32_t *out = a.out + q * a.W;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const uint32_t w = w0 + 32 * c;
+        if (w < a.W) out[w] = dead ? 0u : res[c];
+    }
+}
+
+// Union per repetition from DocBits staged in shared memory (sdb): each set
+// bit of the bucket row, taken 32 buckets at a time, ORs one row of W words
+// (consecutive words per lane: no bank conflicts).
+template <int C>
+__device__ __forceinline__ void expand_unit_smem(const ExpandArgs &a, const uint32_t *sdb,
+                                                 const uint32_t *bm, uint64_t q, uint32_t w0) {
+    uint32_t res[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) res[c] = FULL;
+    bool dead = false;
+    for (uint32_t r = 0; r < a.R && !dead; ++r) {
+        uint32_t o[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) o[c] = 0;
+        bool any = false;
+        const uint32_t lo = r * a.B;
+        for (uint32_t i = 0; i < a.B; i += 32) {
+            const uint32_t bit = lo + i;
+            const uint32_t wi = bit >> 5, sh = bit & 31;
+            uint32_t x = bm[wi];
+            if (sh) x = __funnelshift_r(x, wi + 1 < a.Gw ? bm[wi + 1] : 0u, sh);
+            const uint32_t nb = a.B - i < 32 ? a.B - i : 32;
+            if (nb < 32) x &= (1u << nb) - 1u;
+            any |= x != 0;
+            while (x) {
+                const uint32_t b = i + __ffs(x) - 1;
+                x &= x - 1;
+                const uint32_t *row = sdb + (lo + b) * a.W;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t w = w0 + 32 * c;
+                    if (w < a.W) o[c] |= row[w];
+                }
+            }
+        }
+        uint32_t nz = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            res[c] &= o[c];
+            nz |= res[c];
+        }
+        if (!any || !__any_sync(FULL, nz)) dead = true;
+    }
+    uint32_t *out = a.out + q * a.W;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const uint32_t w = w0 + 32 * c;
+        if (w < a.W) out[w] = dead ? 0u : res[c];
+    }
+}
+
+// One expansion unit: query q's answer words w0, w0+32, .. w0+32*(C-1) from
+// its bucket mask bm.
+template <int C>
+__device__ __forceinline__ void expand_one(const ExpandArgs &a, const uint32_t *bm, uint64_t q,
+                                           uint32_t w0, int lane) {
+    if (a.tab) expand_unit_table<C>(a, bm, q, w0, lane);
+    else expand_unit_sparse<C>(a, bm, q, w0);
+}
+
+template <typename KernelT>
+int blocks_per_sm(KernelT kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
+}
+
+}  // namespace
+}  // namespace rgpu

@@ -23,19 +23,39 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--query-path", type=int, default=0)
     ap.add_argument("--tune", nargs="*", default=[], help="tuning knobs as name=value")
+    ap.add_argument("--tuning-from-cache", action="store_true",
+                    help="use the tuning bench.py cached for this workload's batch")
+    ap.add_argument("--n-docs", type=int, default=None, help="fewer documents (same geometry)")
+    ap.add_argument("--m", type=int, default=None, help="bits per filter (smaller index)")
+    ap.add_argument("--n-queries", type=int, default=None, help="fewer sequence queries (large)")
     a = ap.parse_args(argv)
     import torch
 
     from . import rambo, synth
     if a.workload == "medium":
-        corpus, kmers, q = synth.medium_workload()
+        corpus, kmers, q = synth.medium_workload(n_docs=a.n_docs)
     else:
-        corpus, q = synth.large_workload()
+        kw = {"n_docs": a.n_docs}
+        if a.n_queries:
+            kw["n_queries"] = a.n_queries
+        corpus, q = synth.large_workload(**kw)
         kmers = np.zeros(0, np.uint64)
     p = corpus.params
+    if a.m:
+        p = synth.Params(K=p.K, B=p.B, R=p.R, m=a.m, eta=p.eta, k=p.k, seed=p.seed)
     dev = lambda x, dt: torch.from_numpy(np.ascontiguousarray(x).view(dt)).cuda()
     idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=0)
-    idx.set_tuning(query_path=a.query_path, **{kv.split("=")[0]: int(kv.split("=")[1]) for kv in a.tune})
+    if a.tuning_from_cache:
+        from . import autotune
+        n_kmers = q.n_kmers(p.k) + int(kmers.size)
+        cached = autotune.load_cached(autotune.CACHE_FILE,
+                                      autotune.cache_key(idx, q.n + int(kmers.size), n_kmers))
+        if cached:
+            idx.set_tuning(**cached)
+    else:
+        idx.set_tuning(query_path=a.query_path)
+    if a.tune:
+        idx.set_tuning(**{kv.split("=")[0]: int(kv.split("=")[1]) for kv in a.tune})
     idx.insert_batch_dev(dev(corpus.doc_ids, np.int32), dev(corpus.packed, np.uint8),
                          dev(corpus.offsets, np.int64))
     idx.sync()

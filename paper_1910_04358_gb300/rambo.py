@@ -80,7 +80,11 @@ def load():
             "rambo_query_seqs_noalloc": (i, [p, u64, p, u64, p, p, p]),
             "rambo_query_ranges_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
             "rambo_fold": (i, [p]),
+            "rambo_set_partition": (i, [p, p]),
             "rambo_probed_kmers": (i, [p, C.POINTER(u64), i]),
+            "rambo_insert_words_dev": (i, [p, u32, p, p, u64, p, p, p]),
+            "rambo_query_words_workspace": (sz, [p, u64]),
+            "rambo_query_words_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -110,6 +114,14 @@ def _check_span(packed: np.ndarray, offs: np.ndarray):
     """The host calls read the bytes holding bases [offs[0], offs[-1])."""
     if offs.size and offs[-1] >= offs[0] and packed.size * 4 < int(offs[-1]):
         raise ValueError("packed buffer is shorter than the bases the offsets address")
+
+
+def _out_array(out, n: int, W: int) -> np.ndarray:
+    if out is None:
+        return np.zeros((n, W), dtype=np.uint32)
+    if out.dtype not in (np.uint32, np.int32) or out.shape != (n, W) or not out.flags.c_contiguous:
+        raise ValueError(f"out must be a C-contiguous ({n}, {W}) 32-bit array")
+    return out.view(np.uint32)
 
 
 def _np_ptr(a: np.ndarray):
@@ -234,19 +246,21 @@ class Index:
         _check(load().rambo_insert_batch(self._h, ids.size, _np_ptr(ids), _np_ptr(packed),
                                          _np_ptr(offs)), "rambo_insert_batch")
 
-    def query_kmers(self, kmers) -> np.ndarray:
+    def query_kmers(self, kmers, out: np.ndarray | None = None) -> np.ndarray:
+        """`out` (optional, e.g. pinned): (n, W) uint32 C-contiguous array."""
         km = np.ascontiguousarray(kmers, dtype=np.uint64)
-        out = np.zeros((km.size, self.W), dtype=np.uint32)
+        out = _out_array(out, km.size, self.W)
         _check(load().rambo_query_kmers(self._h, km.size, _np_ptr(km), _np_ptr(out)),
                "rambo_query_kmers")
         return out
 
-    def query_seqs(self, packed, offsets) -> np.ndarray:
+    def query_seqs(self, packed, offsets, out: np.ndarray | None = None) -> np.ndarray:
+        """`out` (optional, e.g. pinned): (n, W) uint32 C-contiguous array."""
         packed = np.ascontiguousarray(packed, dtype=np.uint8)
         offs = np.ascontiguousarray(offsets, dtype=np.uint64)
         _check_span(packed, offs)
         n = max(offs.size - 1, 0)
-        out = np.zeros((n, self.W), dtype=np.uint32)
+        out = _out_array(out, n, self.W)
         _check(load().rambo_query_seqs(self._h, n, _np_ptr(packed), _np_ptr(offs), _np_ptr(out)),
                "rambo_query_seqs")
         return out
@@ -316,6 +330,54 @@ class Index:
 
     def sync(self, stream=None):
         _check(load().rambo_sync(self._h, _stream_handle(stream)), "rambo_sync")
+
+    # -------------------------------------------------- explicit partition
+    def set_partition(self, phi):
+        """phi[d, r] = bucket of document d in repetition r; before any insert."""
+        a = np.ascontiguousarray(phi, dtype=np.uint32)
+        if a.shape != (self.K, self.R):
+            raise ValueError("phi must be (K, R)")
+        _check(load().rambo_set_partition(self._h, _np_ptr(a)), "rambo_set_partition")
+
+    # ------------------------------------------------ documents of words
+    @staticmethod
+    def _word_batch(items):
+        """CSR buffers for a list of items, each a list of byte strings."""
+        import torch
+        words = [w for it in items for w in it]
+        buf = np.frombuffer(b"".join(words) + b"\0" * 8, dtype=np.uint8).copy()
+        term_offs = np.zeros(len(words) + 1, dtype=np.int64)
+        if words:
+            term_offs[1:] = np.cumsum([len(w) for w in words])
+        item_terms = np.zeros(len(items) + 1, dtype=np.int64)
+        item_terms[1:] = np.cumsum([len(it) for it in items])
+        dev = lambda a: torch.from_numpy(a).cuda()
+        return dev(buf), int(term_offs[-1]), dev(term_offs), dev(item_terms)
+
+    def insert_words(self, doc_ids, docs, stream=None):
+        """docs[i]: list of byte strings (the words of document doc_ids[i])."""
+        import torch
+        buf, nbytes, toffs, iterms = self._word_batch(docs)
+        ids = torch.from_numpy(np.ascontiguousarray(doc_ids, dtype=np.uint32).view(np.int32)).cuda()
+        _check(load().rambo_insert_words_dev(self._h, len(docs), _t_ptr(ids), _t_ptr(buf), nbytes,
+                                             _t_ptr(toffs), _t_ptr(iterms), _stream_handle(stream)),
+               "rambo_insert_words_dev")
+        self.sync(stream)
+
+    def query_words(self, queries, stream=None) -> np.ndarray:
+        """queries[i]: list of byte strings; returns (n, W) uint32 masks."""
+        import torch
+        buf, nbytes, toffs, iterms = self._word_batch(queries)
+        n = len(queries)
+        out = torch.empty((n, self.W), dtype=torch.int32, device="cuda")
+        s = _stream_handle(stream)
+        need = int(load().rambo_query_words_workspace(self._h, n))
+        wp, wn = self._workspace(("words", s), need)
+        _check(load().rambo_query_words_dev(self._h, n, _t_ptr(buf), nbytes, _t_ptr(toffs),
+                                            _t_ptr(iterms), _t_ptr(out), wp, wn, s),
+               "rambo_query_words_dev")
+        self.sync(stream)
+        return as_u32(out)
 
     # ------------------------------------------------------------ folding
     def fold(self):

@@ -376,3 +376,33 @@ def stream_workload(n_docs: int | None = None, doc_len: int = 50_000, n_seeds: i
     p = WORKLOAD_PARAMS[STREAM]
     p = Params(K=n_docs or p.K, B=p.B, R=p.R, m=m or p.m, eta=p.eta)
     return StreamWorkload(p, n_seeds, doc_len, 0.01, epoch_docs, queries_per_epoch)
+
+
+# --------------------------------------------------------------------------
+# documents of words (the paper's Section 5.4 document-indexing experiment;
+# the Wiki-dump and ClueWeb09 samples are not available, so documents draw
+# words from a synthetic vocabulary with Zipf-like frequencies)
+
+WORDS = "words"
+WORKLOAD_INDEX[WORDS] = 6
+
+
+def word_vocabulary(rng, n_words: int, mean_len: float = 7.0) -> list[bytes]:
+    """Distinct random lowercase words, lengths 1 + Poisson(mean_len - 1)."""
+    seen, out = set(), []
+    while len(out) < n_words:
+        L = 1 + int(rng.poisson(mean_len - 1))
+        w = bytes(rng.integers(97, 123, size=L).astype(np.uint8))
+        if w not in seen:
+            seen.add(w)
+            out.append(w)
+    return out
+
+
+def word_corpus(rng, K: int, vocab: list[bytes], terms_per_doc: int, zipf_s: float = 1.07):
+    """K documents, each terms_per_doc distinct words drawn with probability
+    proportional to 1 / rank^zipf_s.  Returns a list of index arrays."""
+    ranks = np.arange(1, len(vocab) + 1, dtype=np.float64)
+    p = ranks ** -zipf_s
+    p /= p.sum()
+    return [np.sort(rng.choice(len(vocab), size=terms_per_doc, replace=False, p=p)) for _ in range(K)]

@@ -340,3 +340,57 @@ def test_early_exit_gives_identical_answers_and_probes_fewer_kmers(rambo_lib):
     probed = idx.probed_kmers(reset=True)
     assert np.array_equal(got, want)
     assert 0 < probed < q.n_kmers(p.k)
+
+
+# ------------------------------------------------------ document sharding
+
+def test_sharded_index_equals_composed_single_index_and_oracle(rambo_lib):
+    from paper_1910_04358_gb300 import sharding
+    K, b, R, S = 150, 8, 3, 3
+    p = synth.Params(K=K, B=S * b, R=R, m=1 << 14, eta=2, k=31, seed=4)
+    rng = np.random.default_rng(23)
+    corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=600, sub_rate=0.02)
+    q = synth.sample_queries(rng, corpus, rng.integers(31, 300, size=200), 0.6)
+    sh = sharding.ShardedIndex(K, b, R, p.m, p.eta, p.k, p.seed, shards=S)
+    sh.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
+    got = sh.query_seqs(q.packed, q.offsets)
+    phi = sh.composed_partition()
+    one = rambo_lib.Index(K, S * b, R, p.m, p.eta, p.k, p.seed)
+    one.set_partition(phi)
+    one.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
+    assert np.array_equal(one.query_seqs(q.packed, q.offsets), got)
+    o = oracle.Rambo(K, S * b, R, p.m, p.eta, p.k, p.seed)
+    o.set_partition(phi)
+    o.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
+    assert np.array_equal(o.query_seqs(q.packed, q.offsets), got)
+    with pytest.raises(rambo_lib.RamboError) as e:
+        one.set_partition(phi)  # after inserts
+    assert e.value.code == rambo_lib.RAMBO_ESTATE
+
+
+# --------------------------------------------------- documents of words (5.4)
+
+def test_word_documents_match_oracle(rambo_lib):
+    rng = np.random.default_rng(101)
+    vocab = synth.word_vocabulary(rng, 6000)
+    K, B, R, m, eta = 300, 20, 3, 100_003, 2
+    docs = synth.word_corpus(rng, K, vocab, 150)
+    idx = rambo_lib.Index(K, B, R, m, eta, seed=5)
+    o = oracle.Rambo(K, B, R, m, eta, seed=5)
+    words_of = [[vocab[i] for i in d] for d in docs]
+    # insert in two batches through the device API
+    idx.insert_words(np.arange(0, 150, dtype=np.uint32), words_of[:150])
+    idx.insert_words(np.arange(150, K, dtype=np.uint32), words_of[150:])
+    for d in range(K):
+        o.insert_words(d, words_of[d])
+    assert_index_equal(idx, o, synth.Params(K=K, B=B, R=R, m=m, eta=eta))
+    queries = []
+    for i in range(400):
+        if i % 3:
+            d = int(rng.integers(0, K))
+            queries.append([vocab[j] for j in rng.choice(docs[d], size=int(rng.integers(1, 4)), replace=False)])
+        else:
+            queries.append([vocab[int(j)] for j in rng.integers(0, len(vocab), size=int(rng.integers(1, 3)))])
+    got = idx.query_words(queries)
+    want = np.stack([o.query_words(q) for q in queries])
+    assert np.array_equal(got, want)

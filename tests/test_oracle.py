@@ -395,3 +395,68 @@ def test_fold_equals_index_built_with_half_the_buckets():
     with pytest.raises(oracle.OracleError):
         odd = oracle.Rambo(10, 3, 1, 64, 1, k=5)
         odd.fold()
+
+
+# ---------------------------------------------------- stacked shards (5.3)
+
+def test_stacked_shards_equal_one_rambo_with_composed_bucket_map():
+    # Section 5.3: S node-local RAMBOs of b buckets over disjoint documents
+    # equal one RAMBO of S*b buckets with bucket map b*tau(D) + phi(D); the
+    # global answer is the concatenation of the shards' answers.
+    K, b, R, S = 90, 4, 3, 3
+    p = synth.Params(K=K, B=b, R=R, m=1 << 12, eta=2, k=15)
+    rng = np.random.default_rng(13)
+    corpus = synth.family_corpus(rng, p, n_seeds=6, doc_len=400, sub_rate=0.02)
+    q = synth.sample_queries(rng, corpus, rng.integers(15, 60, size=80), 0.7)
+    tau = np.arange(K) % S
+    shards, members = [], []
+    for s in range(S):
+        mem = np.nonzero(tau == s)[0]
+        o = oracle.Rambo(mem.size, b, R, p.m, p.eta, p.k, p.seed)
+        for li, d in enumerate(mem):
+            o.insert(li, corpus.packed, int(corpus.offsets[d]), int(corpus.offsets[d + 1] - corpus.offsets[d]))
+        shards.append(o)
+        members.append(mem)
+    phi = np.zeros((K, R), dtype=np.uint32)
+    for s, (o, mem) in enumerate(zip(shards, members)):
+        for li, d in enumerate(mem):
+            for r in range(R):
+                phi[d, r] = b * s + o.bucket(li, r)
+    g = oracle.Rambo(K, S * b, R, p.m, p.eta, p.k, p.seed)
+    g.set_partition(phi)
+    g.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
+    want = g.query_seqs(q.packed, q.offsets)
+    for i in range(q.n):
+        b0, b1 = int(q.offsets[i]), int(q.offsets[i + 1])
+        cat = set()
+        for o, mem in zip(shards, members):
+            cat |= {int(mem[li]) for li in oracle.mask_to_docs(o.query_seq(q.packed, b0, b1 - b0))}
+        assert cat == oracle.mask_to_docs(want[i])
+
+
+# ---------------------------------------------------- documents of words (5.4)
+
+def test_word_documents_zero_fn_and_word_positions():
+    # word positions are the general-length hash (pinned above) mod m; a
+    # document's own words always pass, a query of several words passes only
+    # documents containing all of them (up to Bloom and merge false positives)
+    rng = np.random.default_rng(77)
+    vocab = [bytes(rng.integers(97, 123, size=int(L)).astype(np.uint8)) for L in rng.integers(2, 14, 400)]
+    K = 60
+    o = oracle.Rambo(K, 6, 3, 1 << 14, 2, seed=9)
+    docs = [set(rng.choice(len(vocab), size=40, replace=False).tolist()) for _ in range(K)]
+    for d in range(K):
+        o.insert_words(d, [vocab[i] for i in sorted(docs[d])])
+    for w in vocab[:20]:
+        for j in range(2):
+            assert o.word_position(w, j) == oracle.mmh3_x64_128(w, 9 + j)[0] % (1 << 14)
+    for _ in range(100):
+        qs = rng.choice(len(vocab), size=int(rng.integers(1, 4)), replace=False).tolist()
+        got = oracle.mask_to_docs(o.query_words([vocab[i] for i in qs]))
+        truth = {d for d in range(K) if set(qs) <= docs[d]}
+        assert truth <= got
+        # bucket-space identity for word queries
+        inter = set(range(K))
+        for i in qs:
+            inter &= oracle.mask_to_docs(o.query_words([vocab[i]]))
+        assert inter == got
