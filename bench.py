@@ -446,6 +446,13 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
+        # one call per batch: the k-mer part runs on the library's side
+        # stream next to the sequence part (forked from and joined back to
+        # the current stream)
+        idx.query_batch_dev(d_k, d_qp, d_qo, out_kmers=out_k, out_seqs=out_s)
+
+    def step_serial():
+        # the two parts one after the other on one stream (stage breakdown)
         if d_k is not None:
             idx.query_kmers_dev(d_k, out=out_k)
         idx.query_seqs_dev(d_qp, d_qo, out=out_s)
@@ -518,7 +525,17 @@ def run_ours(args):
             torch.cuda.synchronize()
             barrier(world)
             ms_g = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
-            graph = {"ms_per_step": ms_g, "launches_per_step": per_step_launches}
+            # spread: 10 timed replays of one step each
+            singles = []
+            for _ in range(10):
+                ev0.record(gs)
+                g.replay()
+                ev1.record(gs)
+                torch.cuda.synchronize()
+                singles.append(ev0.elapsed_time(ev1))
+            graph = {"ms_per_step": ms_g, "launches_per_step": per_step_launches,
+                     "single_step_ms": {"best": min(singles),
+                                        "median": statistics.median(singles)}}
             if ms_g < ms_step:
                 ms_step = ms_g
                 launches = per_step_launches * args.steps
@@ -528,10 +545,46 @@ def run_ours(args):
             graph["answers_match_eager"] = bool(ok_graph)
         except Exception as ex:
             graph = {"error": repr(ex)}
+    # ---- early exit (the paper's "first FALSE is conclusive", Section 3.3.1;
+    # RAMBO+ sparse evaluation, Section 5.1): identical answers, fewer k-mers
+    # probed.  Reported beside the line, never as `value` (which probes every k-mer).
+    early = None
+    if not args.no_early_exit and q.n and idx.get_tuning()["query_path"] == 1:
+        saved = idx.get_tuning()
+        ref_s = out_s.clone()
+        ref_k = out_k.clone() if out_k is not None else None
+        try:
+            idx.set_tuning(early_exit=1)
+            idx.probed_kmers(reset=True)
+            step()
+            idx.sync()
+            probed = idx.probed_kmers(reset=True)
+            same = torch.equal(out_s, ref_s) and (ref_k is None or torch.equal(out_k, ref_k))
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_ee = ev0.elapsed_time(ev1) / args.steps
+            spk = probe_bytes_per_kmer(info) // SECTOR
+            early = {"ms_per_step": ms_ee, "kmer_queries_per_s": total_kmers / (ms_ee / 1e3),
+                     "seq_kmers_probed": probed, "seq_kmers": n_seq_kmers,
+                     "probed_frac": probed / max(n_seq_kmers, 1),
+                     "index_sectors_per_step": (probed + int(kmers.size)) * spk,
+                     "index_sectors_per_step_without": total_kmers * spk,
+                     "answers_identical": bool(same), "segment": saved["early_exit_segment"]}
+        except Exception as ex:  # report, do not hide
+            early = {"error": repr(ex)}
+        finally:
+            idx.set_tuning(**saved)
+            idx.sync()
     # per-stage breakdown from a separate profiled pass (every stage bracketed)
     idx.profile_reset(timed_stages=STAGES_ALL)
     for _ in range(min(args.steps, 20)):
-        step()
+        step_serial()
     idx.sync()
     prof_all = idx.profile_read()
 
@@ -575,16 +628,12 @@ def run_ours(args):
         pin_os = torch.empty((q.n, idx.W), dtype=torch.int32).pin_memory().numpy()
         e2e_steps = max(3, min(args.steps, 30))
         for _ in range(2):
-            if kmers.size:
-                idx.query_kmers(pin_k, out=pin_ok)
-            idx.query_seqs(pin_p, pin_o, out=pin_os)
+            idx.query_batch(pin_k, pin_p, pin_o, out_kmers=pin_ok, out_seqs=pin_os)
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            if kmers.size:
-                idx.query_kmers(pin_k, out=pin_ok)
-            idx.query_seqs(pin_p, pin_o, out=pin_os)
+            idx.query_batch(pin_k, pin_p, pin_o, out_kmers=pin_ok, out_seqs=pin_os)
         t_e2e = (time.perf_counter() - t0) / e2e_steps
         t_e2e = max_over_ranks(t_e2e, world, dev)
         h2d = int(kmers.nbytes) + int(q.packed.nbytes) + int(q.offsets.nbytes)
@@ -631,6 +680,7 @@ def run_ours(args):
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "spot_check_vs_host_api": ok,
         "launch_mode": launch_mode, "eager_ms_per_step": ms_step_eager, "graph": graph,
         "tuning": idx.get_tuning(), "tuning_source": tuning_source, "serving": serving,
+        "early_exit": early,
         "autotune": ({"trials": len(tuned["trials"]), "best_ms": tuned["ms"]} if tuned else None),
     }
     if rank == 0:
@@ -655,6 +705,7 @@ def main():
     ap.add_argument("--retune", action="store_true", help="autotune even if a cached tuning exists")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-early-exit", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=4000)
     ap.add_argument("--query-path", type=int, default=None,
                     help="0 = prefix/probe/expand launches, 1 = persistent fused launch")

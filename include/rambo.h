@@ -130,8 +130,10 @@ int rambo_insert_batch(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
 
 /* Algorithm 2 for n single k-mers.  kmers[i] is a forward code (first base
  * most significant, 2 bits per base); it is canonicalised inside.  A code
- * with a bit set at or above 2k is RAMBO_EINVAL.  out receives n*W words
- * (query i at out + i*W). */
+ * with a bit set at or above 2k is found on the device: the call still runs
+ * to the end, returns RAMBO_EINVAL and leaves `out` unspecified.  out
+ * receives n*W words (query i at out + i*W).  Same as rambo_query_batch with
+ * no sequences. */
 int rambo_query_kmers(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out);
 
 /* Section 3.3.1 sequence queries: the answer for sequence i (bases
@@ -140,6 +142,18 @@ int rambo_query_kmers(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *o
  * receives n*W words. */
 int rambo_query_seqs(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64_t *base_offsets,
                      uint32_t *out);
+
+/* One batch of both query kinds (either count may be 0): n_kmers single
+ * k-mers as in rambo_query_kmers (answers to out_kmers, n_kmers*W words) and
+ * n_seqs sequences as in rambo_query_seqs (answers to out_seqs, n_seqs*W
+ * words).  The two kinds run concurrently on the GPU, and the k-mers are
+ * pipelined in chunks (tuning knob host_chunk_kmers) so that copies to and
+ * from the host overlap the kernels.  Page-locked host buffers (e.g. from
+ * cudaMallocHost) make every copy asynchronous; pageable buffers work but
+ * serialise the copies.  Synchronous; errors as in the two calls above. */
+int rambo_query_batch(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, uint32_t *out_kmers,
+                      uint64_t n_seqs, const uint8_t *packed, const uint64_t *base_offsets,
+                      uint32_t *out_seqs);
 
 /* ---------------------------------------------------------------------- */
 /* Device-buffer calls: asynchronous on `stream` (a cudaStream_t, NULL =    */
@@ -165,6 +179,20 @@ int rambo_query_kmers_dev(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_
 int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
                          const uint64_t *base_offsets, uint32_t *out, void *workspace,
                          size_t workspace_bytes, void *stream);
+
+/* Device-buffer form of rambo_query_batch: the k-mer part and the sequence
+ * part of one batch, each as in rambo_query_kmers_dev / rambo_query_seqs_dev,
+ * in one workspace of rambo_query_batch_workspace(h, n_kmers, n_seqs) bytes.
+ * With both parts present the k-mer part is forked onto a stream the handle
+ * owns (an event recorded on `stream`) and joined back (`stream` waits for
+ * it), so the parts run concurrently and the call may be captured into a
+ * CUDA graph from `stream`.  Because that side stream belongs to the handle,
+ * two such calls on one handle do not overlap their k-mer parts. */
+size_t rambo_query_batch_workspace(const rambo_t *h, uint64_t n_kmers, uint64_t n_seqs);
+int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, uint32_t *out_kmers,
+                          uint64_t n_seqs, const uint8_t *packed, uint64_t packed_bytes,
+                          const uint64_t *base_offsets, uint32_t *out_seqs, void *workspace,
+                          size_t workspace_bytes, void *stream);
 
 /* Sequence query that allocates nothing.  The paper has no counterpart: this
  * exists for callers that cannot allocate device memory -- hosts that own
@@ -288,6 +316,14 @@ typedef struct {
                                        /* conclusive", Section 5.1 RAMBO+).  Off by    */
                                        /* default: every k-mer is probed               */
     uint32_t early_exit_segment;       /* k-mers between checks (multiple of 128)      */
+    uint32_t kmer_probe_ctas_per_sm;   /* single-k-mer probe grid = SMs x this;        */
+                                       /* 0 = as probe_ctas_per_sm                     */
+    uint32_t host_chunk_kmers;         /* host-buffer calls: k-mers per pipelined      */
+                                       /* chunk (copy in, query, copy out); 0 = about  */
+                                       /* 32 MiB of answers per chunk                  */
+    uint32_t branch_priority;          /* mixed batches: 0 = both kinds at the caller's */
+                                       /* stream priority; 1 = sequences, 2 = k-mers  */
+                                       /* on a stream of the greatest priority        */
 } rambo_tuning_t;
 
 int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out);

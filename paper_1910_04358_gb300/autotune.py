@@ -20,6 +20,7 @@ CACHE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_ca
 
 KNOBS = (
     ("query_path", (0, 1)),
+    ("branch_priority", (0, 1, 2)),
     # expansion variant before its grid: a variant's best grid differs; the
     # filter takes precedence over the nibble table, so it is decided first
     ("expand_filter", (0, 1)),
@@ -28,6 +29,7 @@ KNOBS = (
     ("smem_docbits", (0, 1)),
     ("expand_ctas_per_sm", (2, 4, 8, 16, 32)),
     ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
+    ("kmer_probe_ctas_per_sm", (0, 1, 2, 3, 4)),
     ("fused_tile_kmers", (256, 512, 1024, 2048, 4096)),
     ("fused_short_max", (64, 256, 1024, 4096)),
     ("probe_min_kmers_per_warp", (0, 256, 1024, 4096)),

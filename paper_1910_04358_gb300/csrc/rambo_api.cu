@@ -15,6 +15,11 @@ struct rambo {
     int device;
     int sm_count;
     cudaStream_t stream;     // used by the host-buffer calls
+    cudaStream_t kstream[2]; // k-mer branch of mixed batches (host calls alternate chunks)
+    cudaStream_t pstream[2]; // the same at the device's greatest stream priority
+    cudaEvent_t ev_fork, ev_join, ev_join2;
+    uint64_t *h_offs;        // page-locked staging of rebased host offsets
+    size_t h_offs_bytes;
     uint32_t *d_index;       // m * Gw words
     uint32_t *d_docbits;     // R * B * W words
     uint32_t *d_phi;         // K * R
@@ -149,6 +154,12 @@ int probe_grid(const rambo_t *h) {
     return h->tune.probe_ctas_per_sm ? -(int)(h->sm_count * h->tune.probe_ctas_per_sm) : h->sm_count;
 }
 
+// Grid of the single-k-mer probe: its own knob, else the sequence probe's.
+int kmer_probe_grid(const rambo_t *h) {
+    const uint32_t c = h->tune.kmer_probe_ctas_per_sm;
+    return c ? -(int)(h->sm_count * c) : probe_grid(h);
+}
+
 // (Re)allocates or frees the byte table to match the tuning; the table is
 // rebuilt from the current bitmaps on the handle's stream.  The nibble table
 // (small enough for shared memory) is kept whenever it fits 96 KiB.
@@ -213,9 +224,23 @@ InsWs ins_ws(uint64_t n) {
     return w;
 }
 
+// Waits for the handle's own streams; returns the first error seen.
+cudaError_t sync_own_streams(rambo_t *h) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    for (cudaStream_t ks : h->kstream) {
+        const cudaError_t e2 = cudaStreamSynchronize(ks);
+        if (e == cudaSuccess) e = e2;
+    }
+    for (cudaStream_t ps : h->pstream) {
+        const cudaError_t e2 = cudaStreamSynchronize(ps);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e;
+}
+
 int reserve_stage(rambo_t *h, size_t bytes) {
     if (bytes <= h->stage_bytes) return RAMBO_OK;
-    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    RAMBO_TRY(sync_own_streams(h));
     if (h->d_stage) cudaFree(h->d_stage);
     h->d_stage = nullptr;
     h->stage_bytes = 0;
@@ -280,7 +305,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         qs.segment = h->tune.early_exit_segment;
         qs.probed = h->d_probed;
         {
-            StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
+            StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
             RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s,
                                          qs.tile, qs.short_max));
         }
@@ -290,7 +315,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         return RAMBO_OK;
     }
     {
-        StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
+        StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
         RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
     }
     RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
@@ -346,7 +371,7 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
     a.min_chunk = h->tune.probe_min_kmers_per_warp;
     {
         StageScope sc(h, RAMBO_STAGE_PROBE_KMERS, s, 1);
-        RAMBO_TRY(launch_probe_kmers(a, g, probe_grid(h), s));
+        RAMBO_TRY(launch_probe_kmers(a, g, kmer_probe_grid(h), s));
     }
     ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                      h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
@@ -372,7 +397,7 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
         RAMBO_TRY(launch_register_docs(doc_ids, n, h->d_phi, g.K, g.R, g.B, g.W, h->d_docbits, h->d_err, s));
     }
     {
-        StageScope sc(h, RAMBO_STAGE_PREFIX, s, 3);
+        StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
         RAMBO_TRY(launch_kmer_prefix(offsets, offsets + 1, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
     }
     InsertArgs a{};
@@ -466,6 +491,108 @@ int stage_batch(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64_t *o
     return cuda_rc(e);
 }
 
+int reserve_host_offsets(rambo_t *h, size_t bytes) {
+    if (bytes <= h->h_offs_bytes) return RAMBO_OK;
+    if (h->h_offs) cudaFreeHost(h->h_offs);
+    h->h_offs = nullptr;
+    h->h_offs_bytes = 0;
+    const size_t want = bytes + bytes / 4;
+    void *p = nullptr;
+    RAMBO_TRY(cudaMallocHost(&p, want));
+    h->h_offs = static_cast<uint64_t *>(p);
+    h->h_offs_bytes = want;
+    return RAMBO_OK;
+}
+
+// K-mers per chunk of a host-buffer k-mer batch: about 32 MiB of answers.
+uint64_t host_chunk(const rambo_t *h, uint64_t n) {
+    uint64_t c = h->tune.host_chunk_kmers;
+    if (!c) {
+        c = (32ull << 20) / ((uint64_t)h->g.W * 4 + 8);
+        if (c < (1u << 14)) c = 1u << 14;
+    }
+    return c < n ? c : n;
+}
+
+// Host-buffer mixed batch.  The sequence branch (copy in, query, copy out)
+// runs on the handle's stream; the k-mer branch is cut into chunks that
+// alternate over two more streams, so that one chunk's copies overlap the
+// next chunk's kernels and both branches overlap each other.  Page-locked
+// host buffers make every copy asynchronous; pageable ones still work (the
+// runtime then copies synchronously).  Waits for all of it before returning.
+int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *out_k, uint64_t ns,
+                     const uint8_t *packed, const uint64_t *offs, uint32_t *out_s) {
+    const Geometry &g = h->g;
+    const uint64_t row = (uint64_t)g.W * 4;
+    const uint64_t ck = nk ? host_chunk(h, nk) : 0;
+    const uint64_t nchunks = nk ? (nk + ck - 1) / ck : 0;
+    const int slots = nchunks > 1 ? 2 : (int)nchunks;
+    const size_t kin = align_up(ck * 8), kout = align_up(ck * row);
+    const size_t kslot = kin + kout + kmers_ws(g, ck);
+    uint64_t b_lo = 0, nbytes = 0;
+    size_t p_sz = 0, o_sz = 0, s_out = 0, s_ws = 0;
+    if (ns) {
+        b_lo = offs[0] >> 2;
+        nbytes = ((offs[ns] + 3) >> 2) - b_lo;
+        p_sz = align_up(nbytes + 16);
+        o_sz = align_up((ns + 1) * 8);
+        s_out = align_up(ns * row);
+        s_ws = seq_ws(g, ns).total;
+    }
+    const size_t seq_bytes = p_sz + o_sz + s_out + s_ws;
+    int rc = reserve_stage(h, seq_bytes + (size_t)slots * kslot);
+    if (rc) return rc;
+    if (ns) {
+        if ((rc = reserve_host_offsets(h, (ns + 1) * 8))) return rc;
+        for (uint64_t i = 0; i <= ns; ++i) h->h_offs[i] = offs[i] - 4 * b_lo;
+    }
+    char *base = static_cast<char *>(h->d_stage);
+    // on any failure: wait for what was enqueued, then report
+    auto bail = [&](int code) {
+        sync_own_streams(h);
+        return code;
+    };
+    // branch_priority 1: sequences on a high-priority stream; 2: k-mer chunks
+    cudaStream_t ss = h->tune.branch_priority == 1 ? h->pstream[0] : h->stream;
+    cudaStream_t *ks = h->tune.branch_priority == 2 ? h->pstream : h->kstream;
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e != cudaSuccess) return bail(cuda_rc(e));
+    if (ns && ss != h->stream && (e = cudaStreamWaitEvent(ss, h->ev_fork, 0)) != cudaSuccess)
+        return bail(cuda_rc(e));
+    if (ns) {
+        uint8_t *d_p = reinterpret_cast<uint8_t *>(base);
+        uint64_t *d_o = reinterpret_cast<uint64_t *>(base + p_sz);
+        uint32_t *d_out = reinterpret_cast<uint32_t *>(base + p_sz + o_sz);
+        e = cudaMemcpyAsync(d_p, packed + b_lo, nbytes, cudaMemcpyHostToDevice, ss);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_p + nbytes, 0, 16, ss);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_o, h->h_offs, (ns + 1) * 8, cudaMemcpyHostToDevice, ss);
+        if (e != cudaSuccess) return bail(cuda_rc(e));
+        rc = query_seqs_enqueue(h, ns, d_p, nbytes + 16, d_o, d_o + 1, d_out,
+                                base + p_sz + o_sz + s_out, ss);
+        if (rc) return bail(rc);
+        e = cudaMemcpyAsync(out_s, d_out, ns * row, cudaMemcpyDeviceToHost, ss);
+        if (e != cudaSuccess) return bail(cuda_rc(e));
+    }
+    for (uint64_t c = 0; c < nchunks; ++c) {
+        const int sl = (int)(c & 1);
+        cudaStream_t s = ks[sl];
+        if (c < 2 && (e = cudaStreamWaitEvent(s, h->ev_fork, 0)) != cudaSuccess) return bail(cuda_rc(e));
+        char *slot = base + seq_bytes + (size_t)sl * kslot;
+        const uint64_t i0 = c * ck, cn = ck < nk - i0 ? ck : nk - i0;
+        uint64_t *d_k = reinterpret_cast<uint64_t *>(slot);
+        uint32_t *d_out = reinterpret_cast<uint32_t *>(slot + kin);
+        e = cudaMemcpyAsync(d_k, kmers + i0, cn * 8, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bail(cuda_rc(e));
+        rc = query_kmers_enqueue(h, cn, d_k, d_out, slot + kin + kout, s);
+        if (rc) return bail(rc);
+        e = cudaMemcpyAsync(out_k + i0 * g.W, d_out, cn * row, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return bail(cuda_rc(e));
+    }
+    RAMBO_TRY(sync_own_streams(h));
+    return read_and_clear_err(h);
+}
+
 }  // namespace
 
 extern "C" {
@@ -504,6 +631,18 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     if ((rc = cuda_rc(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device))))
         return fail(rc);
     if ((rc = cuda_rc(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)))) return fail(rc);
+    for (cudaStream_t &ks : h->kstream)
+        if ((rc = cuda_rc(cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking)))) return fail(rc);
+    {
+        int least = 0, greatest = 0;
+        if ((rc = cuda_rc(cudaDeviceGetStreamPriorityRange(&least, &greatest)))) return fail(rc);
+        for (cudaStream_t &ps : h->pstream)
+            if ((rc = cuda_rc(cudaStreamCreateWithPriority(&ps, cudaStreamNonBlocking, greatest))))
+                return fail(rc);
+    }
+    if ((rc = cuda_rc(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)))) return fail(rc);
+    if ((rc = cuda_rc(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)))) return fail(rc);
+    if ((rc = cuda_rc(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming)))) return fail(rc);
     const uint64_t index_bytes = m * (uint64_t)h->g.Gw * 4;
     const uint64_t docbits_bytes = (uint64_t)R * B * h->g.W * 4;
     if ((rc = cuda_rc(cudaMalloc(&h->d_index, index_bytes)))) return fail(rc);
@@ -530,6 +669,9 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.early_exit_segment = 256;
     h->tune.fused_tile_kmers = 1024;
     h->tune.fused_short_max = 1024;
+    h->tune.kmer_probe_ctas_per_sm = 0;
+    h->tune.host_chunk_kmers = 0;
+    h->tune.branch_priority = 0;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -539,6 +681,10 @@ int rambo_destroy(rambo_t *h) {
     if (!h) return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (cudaStream_t ks : h->kstream)
+        if (ks) cudaStreamSynchronize(ks);
+    for (cudaStream_t ps : h->pstream)
+        if (ps) cudaStreamSynchronize(ps);
     cudaFree(h->d_index);
     cudaFree(h->d_docbits);
     cudaFree(h->d_phi);
@@ -552,6 +698,14 @@ int rambo_destroy(rambo_t *h) {
         cudaEventDestroy(p.stop);
     }
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    if (h->h_offs) cudaFreeHost(h->h_offs);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
+    for (cudaStream_t ks : h->kstream)
+        if (ks) cudaStreamDestroy(ks);
+    for (cudaStream_t ps : h->pstream)
+        if (ps) cudaStreamDestroy(ps);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return RAMBO_OK;
@@ -639,6 +793,53 @@ int rambo_query_ranges_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64
                               static_cast<cudaStream_t>(stream));
 }
 
+size_t rambo_query_batch_workspace(const rambo_t *h, uint64_t n_kmers, uint64_t n_seqs) {
+    if (!h) return 0;
+    return (n_kmers ? kmers_ws(h->g, n_kmers) : 0) + (n_seqs ? seq_ws(h->g, n_seqs).total : 0);
+}
+
+int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, uint32_t *out_kmers,
+                          uint64_t n_seqs, const uint8_t *packed, uint64_t packed_bytes,
+                          const uint64_t *base_offsets, uint32_t *out_seqs, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n_kmers == 0 && n_seqs == 0) return RAMBO_OK;
+    if ((n_kmers && (!kmers || !out_kmers)) ||
+        (n_seqs && (n_seqs >= 0xffffffffULL || !base_offsets || !out_seqs || (!packed && packed_bytes))) ||
+        !workspace || workspace_bytes < rambo_query_batch_workspace(h, n_kmers, n_seqs) ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(workspace);
+    if (!n_seqs) return query_kmers_enqueue(h, n_kmers, kmers, out_kmers, w, s);
+    char *wseq = w + (n_kmers ? kmers_ws(h->g, n_kmers) : 0);
+    if (!n_kmers)
+        return query_seqs_enqueue(h, n_seqs, packed, packed_bytes, base_offsets, base_offsets + 1,
+                                  out_seqs, wseq, s);
+    // fork the k-mer branch onto a stream of the handle and join it back, so
+    // that both branches run at once (also inside a stream capture);
+    // branch_priority 1 moves the sequence branch to a high-priority stream
+    // of the handle, 2 puts the k-mer branch on one
+    const uint32_t prio = h->tune.branch_priority;
+    cudaStream_t sk = prio == 2 ? h->pstream[0] : h->kstream[0];
+    cudaStream_t ss = prio == 1 ? h->pstream[1] : s;
+    RAMBO_TRY(cudaEventRecord(h->ev_fork, s));
+    RAMBO_TRY(cudaStreamWaitEvent(sk, h->ev_fork, 0));
+    if (ss != s) RAMBO_TRY(cudaStreamWaitEvent(ss, h->ev_fork, 0));
+    const int rk = query_kmers_enqueue(h, n_kmers, kmers, out_kmers, w, sk);
+    const int rs = query_seqs_enqueue(h, n_seqs, packed, packed_bytes, base_offsets, base_offsets + 1,
+                                      out_seqs, wseq, ss);
+    RAMBO_TRY(cudaEventRecord(h->ev_join, sk));
+    RAMBO_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    if (ss != s) {
+        RAMBO_TRY(cudaEventRecord(h->ev_join2, ss));
+        RAMBO_TRY(cudaStreamWaitEvent(s, h->ev_join2, 0));
+    }
+    return rk ? rk : rs;
+}
+
 int rambo_sync(rambo_t *h, void *stream) {
     if (!h) return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
@@ -678,47 +879,28 @@ int rambo_insert(rambo_t *h, uint32_t doc_id, const uint8_t *packed, uint64_t n_
 }
 
 int rambo_query_kmers(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out) {
-    if (!h) return RAMBO_EINVAL;
-    if (n == 0) return RAMBO_OK;
-    if (!kmers || !out) return RAMBO_EINVAL;
-    const uint64_t bad = h->g.k >= 32 ? 0 : ~((1ULL << (2 * h->g.k)) - 1);
-    for (uint64_t i = 0; i < n; ++i)
-        if (kmers[i] & bad) return RAMBO_EINVAL;
-    DeviceGuard guard(h->device);
-    if (!guard.ok) return RAMBO_ECUDA;
-    const size_t in_sz = align_up(n * 8), out_sz = align_up(n * (uint64_t)h->g.W * 4);
-    int rc = reserve_stage(h, in_sz + out_sz + kmers_ws(h->g, n));
-    if (rc) return rc;
-    char *base = static_cast<char *>(h->d_stage);
-    uint64_t *d_k = reinterpret_cast<uint64_t *>(base);
-    uint32_t *d_out = reinterpret_cast<uint32_t *>(base + in_sz);
-    RAMBO_TRY(cudaMemcpyAsync(d_k, kmers, n * 8, cudaMemcpyHostToDevice, h->stream));
-    rc = query_kmers_enqueue(h, n, d_k, d_out, base + in_sz + out_sz, h->stream);
-    if (rc) return rc;
-    RAMBO_TRY(cudaMemcpyAsync(out, d_out, n * (uint64_t)h->g.W * 4, cudaMemcpyDeviceToHost, h->stream));
-    RAMBO_TRY(cudaStreamSynchronize(h->stream));
-    return read_and_clear_err(h);
+    return rambo_query_batch(h, n, kmers, out, 0, nullptr, nullptr, nullptr);
 }
 
 int rambo_query_seqs(rambo_t *h, uint64_t n, const uint8_t *packed, const uint64_t *base_offsets,
                      uint32_t *out) {
+    return rambo_query_batch(h, 0, nullptr, nullptr, n, packed, base_offsets, out);
+}
+
+int rambo_query_batch(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, uint32_t *out_kmers,
+                      uint64_t n_seqs, const uint8_t *packed, const uint64_t *base_offsets,
+                      uint32_t *out_seqs) {
     if (!h) return RAMBO_EINVAL;
-    if (n == 0) return RAMBO_OK;
-    if (n >= 0xffffffffULL || !base_offsets || !out || !offsets_ok(n, base_offsets)) return RAMBO_EINVAL;
-    if (!packed && base_offsets[n] > base_offsets[0]) return RAMBO_EINVAL;
+    if (n_kmers && (!kmers || !out_kmers)) return RAMBO_EINVAL;
+    if (n_seqs) {
+        if (n_seqs >= 0xffffffffULL || !base_offsets || !out_seqs || !offsets_ok(n_seqs, base_offsets))
+            return RAMBO_EINVAL;
+        if (!packed && base_offsets[n_seqs] > base_offsets[0]) return RAMBO_EINVAL;
+    }
+    if (n_kmers == 0 && n_seqs == 0) return RAMBO_OK;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
-    const size_t out_sz = align_up(n * (uint64_t)h->g.W * 4);
-    Staged st;
-    int rc = stage_batch(h, n, packed, base_offsets, out_sz + seq_ws(h->g, n).total, &st);
-    if (rc) return rc;
-    uint32_t *d_out = reinterpret_cast<uint32_t *>(st.rest);
-    rc = query_seqs_enqueue(h, n, st.packed, st.packed_bytes + 16, st.offsets, st.offsets + 1,
-                            d_out, st.rest + out_sz, h->stream);
-    if (rc) return rc;
-    RAMBO_TRY(cudaMemcpyAsync(out, d_out, n * (uint64_t)h->g.W * 4, cudaMemcpyDeviceToHost, h->stream));
-    RAMBO_TRY(cudaStreamSynchronize(h->stream));
-    return read_and_clear_err(h);
+    return query_batch_host(h, n_kmers, kmers, out_kmers, n_seqs, packed, base_offsets, out_seqs);
 }
 
 // ---------------------------------------------------- documents of words
@@ -911,11 +1093,12 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 1 || t->fused_tile_kmers == 0 ||
         t->fused_tile_kmers > (1u << 24) || t->fused_short_max > (1u << 24) || t->smem_docbits > 1 ||
         t->use_nibble_table > 1 || t->expand_filter > 1 || t->early_exit > 1 ||
-        t->early_exit_segment == 0 || (t->early_exit_segment & 127) || t->early_exit_segment > (1u << 24))
+        t->early_exit_segment == 0 || (t->early_exit_segment & 127) || t->early_exit_segment > (1u << 24) ||
+        t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
-    RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    RAMBO_TRY(sync_own_streams(h));
     h->tune = *t;
     return apply_bytetab(h);
 }

@@ -246,6 +246,8 @@ cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, 
 // Exclusive prefix (n+1 values) of the k-mer counts of items
 // [begins[i], ends[i]); with tile > 0, of the tile counts of the items with
 // more than short_max k-mers (ceil(k-mers / tile); shorter items count 0).
+// Kernels one launch_kmer_prefix of n items enqueues.
+int kmer_prefix_launches(uint64_t n);
 cudaError_t launch_kmer_prefix(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
                                uint64_t packed_bytes, uint64_t *kcum, uint64_t *block_sums,
                                uint32_t *err, cudaStream_t s, uint32_t tile = 0,

@@ -126,6 +126,35 @@ k_prefix_final(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_
     }
 }
 
+// Small batches: the whole scan by one block, SCAN_TILE items per pass (one
+// launch instead of three); kcum[n] = grand total.
+constexpr uint64_t SCAN_SINGLE_MAX = 16 * SCAN_TILE;
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_prefix_single(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
+                uint64_t limit, uint64_t *kcum, uint32_t *err, CountMode cm) {
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < n; base += SCAN_TILE) {
+        const uint64_t i0 = base + (uint64_t)threadIdx.x * SCAN_ITEMS;
+        uint64_t c[SCAN_ITEMS];
+        uint64_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            c[j] = i0 + j < n ? kmer_count(begins, ends, i0 + j, k, limit, err, cm) : 0;
+            sum += c[j];
+        }
+        uint64_t total;
+        uint64_t run = carry + block_exclusive_scan(sum, &total);
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            if (i0 + j < n) kcum[i0 + j] = run;
+            run += c[j];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) kcum[n] = carry;
+}
+
 // ------------------------------------------------------------- registration
 __global__ void k_register(const uint32_t *doc_ids, uint64_t n, const uint32_t *phi, uint32_t K,
                            uint32_t R, uint32_t B, uint32_t W, uint32_t *docbits, uint32_t *err) {
@@ -294,6 +323,8 @@ cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, 
 
 size_t kmer_prefix_block_sums(uint64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
+int kmer_prefix_launches(uint64_t n) { return n == 0 ? 0 : n <= SCAN_SINGLE_MAX ? 1 : 3; }
+
 cudaError_t launch_kmer_prefix(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
                                uint64_t packed_bytes, uint64_t *kcum, uint64_t *block_sums,
                                uint32_t *err, cudaStream_t s, uint32_t tile, uint32_t short_max) {
@@ -301,6 +332,10 @@ cudaError_t launch_kmer_prefix(const uint64_t *begins, const uint64_t *ends, uin
     const uint64_t nblk = kmer_prefix_block_sums(n);
     if (nblk == 0) return cudaSuccess;
     const CountMode cm{tile, short_max};
+    if (n <= SCAN_SINGLE_MAX) {
+        k_prefix_single<<<1, SCAN_THREADS, 0, s>>>(begins, ends, n, k, limit, kcum, err, cm);
+        return cudaGetLastError();
+    }
     k_prefix_partial<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(begins, ends, n, k, limit, block_sums, err, cm);
     k_prefix_blocks<<<1, SCAN_THREADS, 0, s>>>(block_sums, nblk, kcum, n);
     k_prefix_final<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(begins, ends, n, k, limit, block_sums, kcum, cm);

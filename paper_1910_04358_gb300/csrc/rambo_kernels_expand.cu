@@ -115,6 +115,70 @@ __global__ void __launch_bounds__(EXPAND_THREADS) k_expand_nib(ExpandArgs a) {
     }
 }
 
+// Nibble-table expansion for B a multiple of 32 (each repetition's row of
+// the bucket mask is B/32 whole words).  Rows are staged at a power-of-two
+// stride of RWP 16-byte slices (RWP >= ceil(W/4)), every lane owns one slice
+// of one query (RWP lanes per query, 32/RWP queries per warp), and a lookup
+// is a shift, a mask, an add and one 16-byte shared-memory read at an offset
+// known at compile time up to the nibble: no per-lookup branches or
+// multiplies.  The RWP lanes of a query read one contiguous row, so a warp's
+// read takes the minimum 32*16/128 = 4 shared-memory wavefronts.
+template <int RWP>
+__global__ void __launch_bounds__(EXPAND_THREADS) k_expand_nib32(ExpandArgs a) {
+    extern __shared__ uint4 stab4[];
+    constexpr int QPW = 32 / RWP;
+    constexpr uint32_t RS = RWP * 16;  // bytes per staged row
+    constexpr uint32_t SEC = 16 * RS;  // bytes per (repetition, nibble) section
+    const uint32_t rows = a.R * (a.B / 4) * 16;
+    uint32_t *stab = reinterpret_cast<uint32_t *>(stab4);
+    for (uint32_t i = threadIdx.x; i < rows * RWP * 4; i += blockDim.x) {
+        const uint32_t row = i / (RWP * 4), w = i % (RWP * 4);
+        stab[i] = w < a.W ? __ldg(a.ntab + (uint64_t)row * a.W + w) : 0u;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / RWP, ch = lane % RWP;
+    const char *tb = reinterpret_cast<const char *>(stab4) + ch * 16;
+    const uint32_t BW = a.B / 32;  // mask words per repetition
+    const uint32_t w0 = 4u * (uint32_t)ch;
+    const bool vec_store = (a.W & 3u) == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;
+    const uint64_t warp = (uint64_t)blockIdx.x * (EXPAND_THREADS / 32) + threadIdx.x / 32;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (EXPAND_THREADS / 32);
+    for (uint64_t q0 = warp * QPW; q0 < a.n; q0 += nwarps * QPW) {
+        const uint64_t q = q0 + sub;
+        const bool valid = q < a.n;
+        const uint32_t *bm = a.acc + (valid ? q : 0) * a.Gw;
+        uint4 res = make_uint4(FULL, FULL, FULL, FULL);
+        uint32_t off = 0;
+        for (uint32_t r = 0; r < a.R; ++r) {
+            uint4 o = make_uint4(0, 0, 0, 0);
+            for (uint32_t wd = 0; wd < BW; ++wd) {
+                const uint32_t chunk = valid ? __ldg(bm + r * BW + wd) : 0u;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const uint4 x = *reinterpret_cast<const uint4 *>(
+                        tb + off + t * SEC + ((chunk >> (4 * t)) & 15u) * RS);
+                    o.x |= x.x; o.y |= x.y; o.z |= x.z; o.w |= x.w;
+                }
+                off += 8 * SEC;
+            }
+            res.x &= o.x; res.y &= o.y; res.z &= o.z; res.w &= o.w;
+        }
+        if (valid && w0 < a.W) {
+            uint32_t *out = a.out + q * a.W + w0;
+            if (vec_store) {
+                *reinterpret_cast<uint4 *>(out) = res;
+            } else {
+                const uint32_t left = a.W - w0;
+                out[0] = res.x;
+                if (left > 1) out[1] = res.y;
+                if (left > 2) out[2] = res.z;
+                if (left > 3) out[3] = res.w;
+            }
+        }
+    }
+}
+
 // Expansion by candidate filtering (the paper's sparse evaluation, Section
 // 5.1 "Query time speedup", applied per document): the union of repetition 0
 // is formed from the nibble table (its repetition-0 rows staged in shared
@@ -261,8 +325,39 @@ cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cud
         else k_expand_filter<1><<<(unsigned)max_blocks, EXPAND_THREADS, filt_bytes, s>>>(a);
         return cudaGetLastError();
     }
-    // nibble table in shared memory (small K): several queries per warp
+    // nibble table in shared memory (small K), B a multiple of 32: rows at a
+    // power-of-two stride, one 16-byte slice per lane
     const uint32_t rw = (a.W + 3) / 4;
+    uint32_t rwp = 1;
+    while (rwp < rw) rwp <<= 1;
+    const size_t nib32_bytes = (size_t)a.R * (a.B / 4) * 16 * rwp * 16;
+    if (a.ntab && a.B % 32 == 0 && rwp <= 32 && nib32_bytes <= SMEM_NIBTAB_MAX &&
+        a.n >= (uint64_t)sm_count * 64) {
+        cudaError_t e2 = cudaSuccess;
+#define RGPU_NIB32(P)                                                                              \
+    if (rwp == P) {                                                                                \
+        if (nib32_bytes > 48 * 1024)                                                               \
+            e2 = cudaFuncSetAttribute(k_expand_nib32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)nib32_bytes);                                           \
+        int occ = 1;                                                                               \
+        if (e2 == cudaSuccess)                                                                     \
+            e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expand_nib32<P>,            \
+                                                               EXPAND_THREADS, nib32_bytes);       \
+        const int grid = occ * sm_count < max_blocks ? occ * sm_count : max_blocks;                \
+        if (e2 == cudaSuccess)                                                                     \
+            k_expand_nib32<P><<<grid > 0 ? grid : 1, EXPAND_THREADS, nib32_bytes, s>>>(a);          \
+    }
+        RGPU_NIB32(1)
+        RGPU_NIB32(2)
+        RGPU_NIB32(4)
+        RGPU_NIB32(8)
+        RGPU_NIB32(16)
+        RGPU_NIB32(32)
+#undef RGPU_NIB32
+        if (e2 != cudaSuccess) return e2;
+        return cudaGetLastError();
+    }
+    // nibble table in shared memory (small K): several queries per warp
     const size_t nib_bytes = (size_t)a.R * ((a.B + 3) / 4) * 16 * rw * 16;
     if (a.ntab && rw <= 32 && nib_bytes <= SMEM_NIBTAB_MAX && a.n >= (uint64_t)sm_count * 64) {
         // rw <= 32 slices -> at most 32 lanes of one slice

@@ -85,6 +85,9 @@ def load():
             "rambo_insert_words_dev": (i, [p, u32, p, p, u64, p, p, p]),
             "rambo_query_words_workspace": (sz, [p, u64]),
             "rambo_query_words_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
+            "rambo_query_batch": (i, [p, u64, p, p, u64, p, p, p]),
+            "rambo_query_batch_workspace": (sz, [p, u64, u64]),
+            "rambo_query_batch_dev": (i, [p, u64, p, p, u64, p, u64, p, p, p, sz, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -163,7 +166,8 @@ STAGES = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
 TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_per_sm",
                  "use_byte_table", "byte_table_max_mb", "query_path", "fused_tile_kmers",
                  "fused_short_max", "smem_docbits", "use_nibble_table",
-                 "expand_filter", "early_exit", "early_exit_segment")
+                 "expand_filter", "early_exit", "early_exit_segment",
+                 "kmer_probe_ctas_per_sm", "host_chunk_kmers", "branch_priority")
 
 
 class _Tuning(C.Structure):
@@ -265,6 +269,22 @@ class Index:
                "rambo_query_seqs")
         return out
 
+    def query_batch(self, kmers, packed, offsets, out_kmers: np.ndarray | None = None,
+                    out_seqs: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray]:
+        """Single k-mers and sequences in one call (both kinds run concurrently,
+        copies pipelined); returns (k-mer answers, sequence answers)."""
+        km = np.ascontiguousarray(kmers, dtype=np.uint64)
+        packed = np.ascontiguousarray(packed, dtype=np.uint8)
+        offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+        _check_span(packed, offs)
+        ns = max(offs.size - 1, 0)
+        out_kmers = _out_array(out_kmers, km.size, self.W)
+        out_seqs = _out_array(out_seqs, ns, self.W)
+        _check(load().rambo_query_batch(self._h, km.size, _np_ptr(km), _np_ptr(out_kmers), ns,
+                                        _np_ptr(packed), _np_ptr(offs) if ns else None,
+                                        _np_ptr(out_seqs)), "rambo_query_batch")
+        return out_kmers, out_seqs
+
     # ----------------------------------------------------- device buffers
     def _workspace(self, stream_key, nbytes):
         ws = self._ws.get(stream_key)
@@ -313,6 +333,30 @@ class Index:
                                            _t_ptr(offsets), _t_ptr(out), wp, wn, s),
                "rambo_query_seqs_dev")
         return out
+
+    def query_batch_dev(self, kmers, packed, offsets, out_kmers=None, out_seqs=None, stream=None,
+                        workspace=None):
+        """Device form of query_batch: kmers int64, packed uint8, offsets int64
+        (n+1) CUDA tensors; the k-mer part runs on a side stream joined back
+        to `stream`.  Returns (k-mer answers, sequence answers) (n, W) int32."""
+        import torch
+        nk = kmers.numel() if kmers is not None else 0
+        ns = max(offsets.numel() - 1, 0) if offsets is not None else 0
+        dev = (kmers if kmers is not None else offsets).device
+        if out_kmers is None:
+            out_kmers = torch.empty((nk, self.W), dtype=torch.int32, device=dev)
+        if out_seqs is None:
+            out_seqs = torch.empty((ns, self.W), dtype=torch.int32, device=dev)
+        need = int(load().rambo_query_batch_workspace(self._h, nk, ns))
+        s = _stream_handle(stream)
+        wp, wn = workspace if workspace is not None else self._workspace(s, need)
+        _check(load().rambo_query_batch_dev(
+            self._h, nk, _t_ptr(kmers) if nk else None, _t_ptr(out_kmers) if nk else None, ns,
+            _t_ptr(packed) if ns and packed is not None else None,
+            packed.numel() if ns and packed is not None else 0,
+            _t_ptr(offsets) if ns else None, _t_ptr(out_seqs) if ns else None, wp, wn, s),
+            "rambo_query_batch_dev")
+        return out_kmers, out_seqs
 
     def query_ranges_dev(self, packed, begins, ends, out=None, stream=None, workspace=None):
         """Items [begins[i], ends[i]) of a packed uint8 CUDA tensor (int64 tensors)."""

@@ -303,9 +303,16 @@ def test_fold_matches_oracle_and_direct_half_index(rambo_lib, K, B, R, m):
     assert np.array_equal(direct.copy_index(), idx.copy_index())
 
 
-def test_expansion_variants_on_many_kmer_queries(rambo_lib):
+@pytest.mark.parametrize("K,B,R", [
+    (700, 32, 4),    # B % 32 == 0: power-of-two row kernel, W % 4 != 0 (scalar stores)
+    (1000, 32, 3),   # ... W % 4 == 0 (16-byte stores)
+    (1024, 64, 2),   # two mask words per repetition
+    (100, 32, 3),    # one 16-byte slice per row (32 queries per warp)
+    (1000, 24, 3),   # B % 32 != 0: generic nibble kernel
+])
+def test_expansion_variants_on_many_kmer_queries(rambo_lib, K, B, R):
     # enough queries per block that the shared-memory variants engage
-    p = synth.Params(K=700, B=32, R=4, m=1 << 14, eta=2, k=31, seed=12)
+    p = synth.Params(K=K, B=B, R=R, m=1 << 14, eta=2, k=31, seed=12)
     rng = np.random.default_rng(31)
     corpus = synth.family_corpus(rng, p, n_seeds=30, doc_len=600, sub_rate=0.02)
     kmers = synth.sample_kmers(rng, corpus, 12_000, p.k, 0.5)
@@ -314,6 +321,7 @@ def test_expansion_variants_on_many_kmer_queries(rambo_lib):
     idx = gpu_index(rambo_lib, p, corpus)
     for st in (dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=1),
                dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=0),
+               dict(expand_ctas_per_sm=8, use_nibble_table=1, expand_filter=0),
                dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=1),
                dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=0, use_byte_table=1),
                dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=0, use_byte_table=0)):
@@ -321,6 +329,104 @@ def test_expansion_variants_on_many_kmer_queries(rambo_lib):
         got = idx.query_kmers_dev(_dev(kmers, np.int64))
         idx.sync()
         assert np.array_equal(rambo_lib.as_u32(got), want), st
+
+
+def test_sequence_batch_past_single_block_scan(rambo_lib):
+    # more than 16 * 4096 sequences: the k-mer prefix takes the three-launch
+    # multi-block scan instead of the single-block one
+    p = synth.Params(K=64, B=8, R=2, m=1 << 13, eta=2, k=31, seed=6)
+    rng = np.random.default_rng(44)
+    corpus = synth.family_corpus(rng, p, n_seeds=8, doc_len=400, sub_rate=0.02)
+    q = synth.sample_queries(rng, corpus, rng.integers(0, 60, size=70_000), 0.5)
+    o = oracle_index(p, corpus)
+    want = o.query_seqs(q.packed, q.offsets)
+    idx = gpu_index(rambo_lib, p, corpus)
+    for path in (0, 1):
+        idx.set_tuning(query_path=path)
+        assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want), path
+
+
+# ------------------------------------------------ mixed batches (both kinds)
+
+def _mixed_case(seed=5):
+    p = synth.Params(K=300, B=16, R=3, m=1 << 14, eta=2, k=31, seed=seed)
+    rng = np.random.default_rng(seed)
+    corpus = synth.family_corpus(rng, p, n_seeds=15, doc_len=800, sub_rate=0.02)
+    kmers = synth.sample_kmers(rng, corpus, 7_001, p.k, 0.5)
+    q = synth.sample_queries(rng, corpus, rng.integers(0, 400, size=257), 0.5)
+    return p, corpus, kmers, q
+
+
+def test_query_batch_host_pipelined_chunks_match_oracle(rambo_lib):
+    p, corpus, kmers, q = _mixed_case()
+    o = oracle_index(p, corpus)
+    want_k = o.query_kmers(kmers, threads=4)
+    want_s = o.query_seqs(q.packed, q.offsets)
+    idx = gpu_index(rambo_lib, p, corpus)
+    for chunk in (0, 1000, 7_001, 3):  # auto, ragged last chunk, one chunk, many
+        for path in (0, 1):
+            for prio in (0, 1, 2):
+                idx.set_tuning(host_chunk_kmers=chunk, query_path=path, branch_priority=prio)
+                got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets)
+                assert np.array_equal(got_k, want_k), (chunk, path, prio)
+                assert np.array_equal(got_s, want_s), (chunk, path, prio)
+    idx.set_tuning(branch_priority=0)
+    # either part may be empty; the single-kind calls go through the same path
+    idx.set_tuning(host_chunk_kmers=1000)
+    got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets[:1])
+    assert np.array_equal(got_k, want_k) and got_s.shape == (0, idx.W)
+    got_k, got_s = idx.query_batch(kmers[:0], q.packed, q.offsets)
+    assert np.array_equal(got_s, want_s) and got_k.shape == (0, idx.W)
+    assert np.array_equal(idx.query_kmers(kmers), want_k)
+    assert np.array_equal(idx.query_seqs(q.packed, q.offsets), want_s)
+
+
+def test_query_batch_host_rejects_bad_kmer_code_after_running(rambo_lib):
+    p, corpus, kmers, q = _mixed_case()
+    idx = gpu_index(rambo_lib, p, corpus)
+    bad = kmers.copy()
+    bad[123] |= np.uint64(1) << np.uint64(2 * p.k)
+    with pytest.raises(rambo_lib.RamboError):
+        idx.query_batch(bad, q.packed, q.offsets)
+    # the error is cleared: the next call succeeds
+    o = oracle_index(p, corpus)
+    assert np.array_equal(idx.query_kmers(kmers), o.query_kmers(kmers, threads=4))
+
+
+def test_query_batch_dev_and_graph_capture_match_oracle(rambo_lib):
+    torch = _torch()
+    p, corpus, kmers, q = _mixed_case(seed=8)
+    o = oracle_index(p, corpus)
+    want_k = o.query_kmers(kmers, threads=4)
+    want_s = o.query_seqs(q.packed, q.offsets)
+    idx = gpu_index(rambo_lib, p, corpus)
+    d_k, d_p = _dev(kmers, np.int64), _dev(q.packed, np.uint8)
+    d_o = _dev(q.offsets.astype(np.uint64), np.int64)
+    for path in (0, 1):
+        for prio in (0, 1, 2):
+            idx.set_tuning(query_path=path, branch_priority=prio)
+            ok, os_ = idx.query_batch_dev(d_k, d_p, d_o)
+            idx.sync()
+            assert np.array_equal(rambo_lib.as_u32(ok), want_k), (path, prio)
+            assert np.array_equal(rambo_lib.as_u32(os_), want_s), (path, prio)
+    # captured once, replayed twice into zeroed outputs
+    for prio in (0, 1, 2):
+        idx.set_tuning(branch_priority=prio)
+        out_k = torch.zeros((kmers.size, idx.W), dtype=torch.int32, device="cuda")
+        out_s = torch.zeros((q.n, idx.W), dtype=torch.int32, device="cuda")
+        idx.query_batch_dev(d_k, d_p, d_o, out_kmers=out_k, out_seqs=out_s)
+        idx.sync()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            idx.query_batch_dev(d_k, d_p, d_o, out_kmers=out_k, out_seqs=out_s)
+        for _ in range(2):
+            out_k.zero_()
+            out_s.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert np.array_equal(rambo_lib.as_u32(out_k), want_k), prio
+            assert np.array_equal(rambo_lib.as_u32(out_s), want_s), prio
+        idx.sync()
 
 
 def test_early_exit_gives_identical_answers_and_probes_fewer_kmers(rambo_lib):
