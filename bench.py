@@ -37,7 +37,8 @@ UNIT = "k-mer queries/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 CSRC = os.path.join(ROOT, "paper_1910_04358_gb300", "csrc")
-KERNEL_SRC = {"k_fused": "rambo_kernels_fused.cu", "k_probe_seqs": "rambo_kernels_probe.cu"}
+KERNEL_SRC = {"k_fused": "rambo_kernels_fused.cu", "k_probe_seqs": "rambo_kernels_probe.cu",
+              "k_binned": "rambo_kernels_binned.cu"}
 SECTOR = 32
 STAGES_ALL = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
 
@@ -154,6 +155,17 @@ def probe_bytes_per_kmer(info) -> int:
     """eta position groups per k-mer, each rounded up to whole 32-byte sectors."""
     g = info["group_bytes"]
     return info["eta"] * SECTOR * ((g + SECTOR - 1) // SECTOR)
+
+
+def effective_path(tuning, info) -> int:
+    """Sequence query path the library takes for this tuning and geometry (the
+    binding always passes a workspace large enough for path 2)."""
+    g = info["group_bytes"]
+    if tuning["query_path"] == 2 and g <= 16:
+        return 2
+    if tuning["query_path"] >= 1 and g <= 512:
+        return 1
+    return 0
 
 
 def probe_algorithmic_bytes(info, n_kmers: int, n_queries: int, n_bases: int) -> int:
@@ -549,12 +561,12 @@ def run_ours(args):
     # RAMBO+ sparse evaluation, Section 5.1): identical answers, fewer k-mers
     # probed.  Reported beside the line, never as `value` (which probes every k-mer).
     early = None
-    if not args.no_early_exit and q.n and idx.get_tuning()["query_path"] == 1:
+    if not args.no_early_exit and q.n:
         saved = idx.get_tuning()
         ref_s = out_s.clone()
         ref_k = out_k.clone() if out_k is not None else None
         try:
-            idx.set_tuning(early_exit=1)
+            idx.set_tuning(early_exit=1, query_path=1)  # early exit is a fused-path option
             idx.probed_kmers(reset=True)
             step()
             idx.sync()
@@ -596,15 +608,21 @@ def run_ours(args):
     dom = "probe_seqs" if q.n else "probe_kmers"
     dom_ms = prof[dom]["ms"] / max(prof[dom]["timed"], 1)
     alg_bytes = probe_algorithmic_bytes(info, n_seq_kmers, q.n, q.n_bases)
-    fused = idx.get_tuning()["query_path"] == 1
-    if fused:  # the fused launch also writes the answer masks
+    path = effective_path(idx.get_tuning(), info)
+    if path == 1:  # the fused launch also writes the answer masks
         alg_bytes += q.n * idx.W * 4
     peak, peak_src = measured_peak_gbs()
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-    traffic = measured_traffic(args.workload, "k_fused" if fused else "k_probe_seqs")
+    src_key = {0: "k_probe_seqs", 1: "k_fused", 2: "k_binned"}[path]
+    traffic = measured_traffic(args.workload, src_key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_fused_prep+k_fused" if fused else "k_probe_seqs",
+                "frac_of_spec_7900": achieved / 7900.0,
+                "dram_bytes_per_kmer": (traffic / n_seq_kmers) if traffic and n_seq_kmers else None,
+                "random_line_ceiling": "45-51 G random 128-byte lines/s measured "
+                                       "(profiles/k_gather_random_records.md)",
+                "kernel": {0: "k_probe_seqs", 1: "k_fused_prep+k_fused",
+                           2: "k_bin_scatter+k_bin_chunks+k_bin_probe"}[path],
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "bytes_per_kmer": probe_bytes_per_kmer(info), "avg_launch_ms": dom_ms,
                 "peak_source": peak_src}
@@ -660,10 +678,17 @@ def run_ours(args):
         while spent < 10.0 and reps < 200:
             spent += time_oracle(o, ks, sp, so, threads)
             reps += 1
+        # one host thread on the same sample (a few repetitions)
+        reps1, spent1 = 0, 0.0
+        while spent1 < 3.0 and reps1 < 50:
+            spent1 += time_oracle(o, ks, sp, so, 1)
+            reps1 += 1
         cpu = {"value": units * reps / spent, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{ks.size} single k-mers + {so.size - 1} sequences ({units} k-mers) "
                          f"x {reps} repetitions; restricted-mode oracle index "
-                         f"(tracks the sample's probe positions), built in {obuild:.1f} s"}
+                         f"(tracks the sample's probe positions), built in {obuild:.1f} s",
+               "single_thread": {"value": units * reps1 / spent1, "unit": UNIT,
+                                 "repetitions": reps1}}
 
     clk = clocks.summary(t_wall0, t_wall1)
     line = {

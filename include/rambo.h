@@ -167,6 +167,12 @@ int rambo_query_batch(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, uint3
 size_t rambo_insert_workspace(const rambo_t *h, uint64_t n_docs);
 size_t rambo_query_kmers_workspace(const rambo_t *h, uint64_t n);
 size_t rambo_query_seqs_workspace(const rambo_t *h, uint64_t n);
+/* Workspace with which a batch of n sequences over packed_bytes bytes can
+ * take the tuned query path: query_path 2 (region-binned probing) needs room
+ * for its probe records and runs only when the workspace passed to the call
+ * is at least this large; with less (down to rambo_query_seqs_workspace) the
+ * call takes path 1.  Same answers either way. */
+size_t rambo_query_seqs_workspace_for(const rambo_t *h, uint64_t n, uint64_t packed_bytes);
 
 int rambo_insert_batch_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
                            const uint8_t *packed, uint64_t packed_bytes,
@@ -182,13 +188,16 @@ int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t
 
 /* Device-buffer form of rambo_query_batch: the k-mer part and the sequence
  * part of one batch, each as in rambo_query_kmers_dev / rambo_query_seqs_dev,
- * in one workspace of rambo_query_batch_workspace(h, n_kmers, n_seqs) bytes.
+ * in one workspace of rambo_query_batch_workspace(h, n_kmers, n_seqs,
+ * packed_bytes) bytes (the k-mer part first; a smaller one down to the two
+ * parts' minimum sizes is accepted, as for rambo_query_seqs_workspace_for).
  * With both parts present the k-mer part is forked onto a stream the handle
  * owns (an event recorded on `stream`) and joined back (`stream` waits for
  * it), so the parts run concurrently and the call may be captured into a
  * CUDA graph from `stream`.  Because that side stream belongs to the handle,
  * two such calls on one handle do not overlap their k-mer parts. */
-size_t rambo_query_batch_workspace(const rambo_t *h, uint64_t n_kmers, uint64_t n_seqs);
+size_t rambo_query_batch_workspace(const rambo_t *h, uint64_t n_kmers, uint64_t n_seqs,
+                                   uint64_t packed_bytes);
 int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, uint32_t *out_kmers,
                           uint64_t n_seqs, const uint8_t *packed, uint64_t packed_bytes,
                           const uint64_t *base_offsets, uint32_t *out_seqs, void *workspace,
@@ -298,7 +307,11 @@ typedef struct {
     uint32_t query_path;               /* sequence queries: 0 = prefix scan + probe +  */
                                        /* expand launches; 1 = persistent fused launch */
                                        /* with length-bucketed work queues (groups up  */
-                                       /* to 512 B; otherwise path 0 is used)          */
+                                       /* to 512 B; otherwise path 0 is used); 2 =     */
+                                       /* region-binned probing (groups up to 16 B and */
+                                       /* a workspace from                             */
+                                       /* rambo_query_seqs_workspace_for; otherwise    */
+                                       /* path 1)                                      */
     uint32_t fused_tile_kmers;         /* path 1: k-mers per tile of a long query      */
     uint32_t fused_short_max;          /* path 1: queries with at most this many       */
                                        /* k-mers are probed and expanded by one warp   */
@@ -320,11 +333,18 @@ typedef struct {
                                        /* 0 = as probe_ctas_per_sm                     */
     uint32_t host_chunk_kmers;         /* host-buffer calls: k-mers per pipelined      */
                                        /* chunk (copy in, query, copy out); 0 = about  */
-                                       /* 32 MiB of answers per chunk                  */
+                                       /* 16 MiB of answers per chunk; the first chunk */
+                                       /* is a quarter of it                           */
     uint32_t branch_priority;          /* mixed batches: 0 = both kinds at the caller's */
                                        /* stream priority; 1 = sequences, 2 = k-mers  */
                                        /* on a stream of the greatest priority        */
+    uint32_t host_slots;               /* host-buffer calls: k-mer chunks in flight    */
+                                       /* (1..RAMBO_MAX_HOST_SLOTS; default 3)         */
+    uint32_t bin_region_kib;           /* path 2: index bytes per region (KiB; 0 =     */
+                                       /* 32768); regions hold a power-of-two number   */
+                                       /* of groups and are at most 4096              */
 } rambo_tuning_t;
+#define RAMBO_MAX_HOST_SLOTS 4
 
 int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out);
 /* Applies new knobs after waiting for the handle's stream; RAMBO_EINVAL if a
@@ -343,6 +363,15 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t);
 int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t record_bytes,
                        uint64_t n_probes, uint32_t load_variant, uint32_t unroll, uint64_t seed,
                        void *sink, void *stream);
+
+/* Copies `bytes` (a multiple of 16) from device memory `src` into page-locked
+ * host memory `dst_host` with 16-byte stores issued by SMs_count x
+ * blocks_per_sm blocks (SM-driven copy-out over the host link, to compare
+ * with the copy engine).  RAMBO_EINVAL if dst_host is not device-addressable
+ * page-locked host memory (cudaHostAlloc, cudaMallocHost, registered) or an
+ * argument is out of range.  Asynchronous on `stream`. */
+int rambo_probe_host_write(const void *src, void *dst_host, uint64_t bytes, uint32_t blocks_per_sm,
+                           void *stream);
 
 /* Reads (into *previous) and, if bytes > 0, sets the current context's L2
  * fetch granularity limit (32, 64 or 128 bytes).  A per-process context

@@ -19,7 +19,7 @@ import os
 CACHE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 
 KNOBS = (
-    ("query_path", (0, 1)),
+    ("query_path", (0, 1, 2)),
     ("branch_priority", (0, 1, 2)),
     # expansion variant before its grid: a variant's best grid differs; the
     # filter takes precedence over the nibble table, so it is decided first

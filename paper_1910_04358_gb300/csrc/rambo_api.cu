@@ -15,8 +15,9 @@ struct rambo {
     int device;
     int sm_count;
     cudaStream_t stream;     // used by the host-buffer calls
-    cudaStream_t kstream[2]; // k-mer branch of mixed batches (host calls alternate chunks)
-    cudaStream_t pstream[2]; // the same at the device's greatest stream priority
+    cudaStream_t kstream[RAMBO_MAX_HOST_SLOTS];  // k-mer branch of mixed batches (host calls
+                                                 // rotate chunks over them)
+    cudaStream_t pstream[RAMBO_MAX_HOST_SLOTS];  // the same at the device's greatest priority
     cudaEvent_t ev_fork, ev_join, ev_join2;
     uint64_t *h_offs;        // page-locked staging of rebased host offsets
     size_t h_offs_bytes;
@@ -45,6 +46,25 @@ struct rambo {
 };
 
 namespace rgpu {
+
+void *mapped_host_range(const void *p, uint64_t bytes) {
+    if (!p || !bytes) return nullptr;
+    const char *first = static_cast<const char *>(p);
+    const char *last = first + (bytes - 1);
+    cudaPointerAttributes a0{}, a1{};
+    if (cudaPointerGetAttributes(&a0, first) != cudaSuccess ||
+        cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+        cudaGetLastError();  // an unknown pointer leaves a (non-sticky) error behind
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer ||
+        !a1.devicePointer)
+        return nullptr;
+    if (static_cast<const char *>(a1.devicePointer) - static_cast<const char *>(a0.devicePointer) !=
+        static_cast<ptrdiff_t>(bytes - 1))
+        return nullptr;
+    return a0.devicePointer;
+}
 
 Geometry make_geometry(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint32_t k,
                        uint64_t seed) {
@@ -213,6 +233,37 @@ SeqWs seq_ws(const Geometry &g, uint64_t n) {
 
 size_t kmers_ws(const Geometry &g, uint64_t n) { return align_up(n * (uint64_t)g.Gw * 4); }
 
+// Extra workspace of the region-binned path (after the sequence layout): bin
+// counters, the work-item prefix and nb bins of cap records.  A bin holds
+// 1/8 more than its expected share of a batch whose k-mers are at most the
+// bases of packed_bytes (plus 1024), so with hashed positions records almost
+// never spill into the direct-probe path.
+struct BinLayout {
+    uint32_t nb, shift;
+    uint64_t cap;
+    size_t count_off, pre_off, rec_off, bytes;
+};
+BinLayout bin_layout(const rambo_t *h, uint64_t packed_bytes) {
+    const Geometry &g = h->g;
+    BinLayout L{};
+    const uint64_t region = (uint64_t)(h->tune.bin_region_kib ? h->tune.bin_region_kib : 32768) << 10;
+    L.nb = binned_bins(g, region, &L.shift);
+    const uint64_t expect = (4 * packed_bytes * g.eta + L.nb - 1) / L.nb;
+    L.cap = expect + expect / 8 + 1024;
+    L.count_off = 0;
+    L.pre_off = align_up((size_t)L.nb * 8);
+    L.rec_off = L.pre_off + align_up(((size_t)L.nb + 1) * 8);
+    L.bytes = L.rec_off + (size_t)L.nb * L.cap * 8;
+    return L;
+}
+bool use_binned(const rambo_t *h) { return h->tune.query_path == 2 && binned_supported(h->g); }
+// Sequence workspace that lets the tuned path run on a batch over packed_bytes.
+size_t seq_ws_for(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
+    size_t t = seq_ws(h->g, n).total;
+    if (use_binned(h)) t += bin_layout(h, packed_bytes).bytes;
+    return t;
+}
+
 struct InsWs {
     size_t kcum, bsum, total;
 };
@@ -265,7 +316,7 @@ Aligned align_packed(const uint8_t *packed, uint64_t packed_bytes) {
 // Items are [begins[i], ends[i]); a CSR batch passes (offsets, offsets + 1).
 int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
                        const uint64_t *offsets, const uint64_t *ends, uint32_t *out, void *ws,
-                       cudaStream_t s) {
+                       size_t ws_bytes, cudaStream_t s) {
     const Geometry &g = h->g;
     const SeqWs L = seq_ws(g, n);
     char *w = static_cast<char *>(ws);
@@ -273,7 +324,54 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     uint64_t *bsum = reinterpret_cast<uint64_t *>(w + L.bsum);
     uint32_t *acc = reinterpret_cast<uint32_t *>(w + L.acc);
     const Aligned al = align_packed(packed, packed_bytes);
-    if (h->tune.query_path == 1 && fused_supported(g)) {
+    if (use_binned(h)) {
+        const BinLayout B = bin_layout(h, packed_bytes);
+        if (ws_bytes >= L.total + B.bytes) {
+            // region-binned probing: records binned by index region, probed
+            // region by region (L2 holds a region), then the expansion
+            {
+                StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
+                RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
+            }
+            RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
+            BinnedArgs ba{};
+            ProbeArgs &a = ba.p;
+            a.index = h->d_index;
+            a.m = g.m;
+            a.m_pow2 = (g.m & (g.m - 1)) == 0;
+            a.Gw = g.Gw;
+            a.eta = g.eta;
+            a.k = g.k;
+            a.seed32 = (uint32_t)g.seed;
+            a.packed = al.p;
+            a.packed_bytes = al.bytes;
+            a.base_shift = al.base_shift;
+            a.offsets = offsets;
+            a.ends = ends;
+            a.kcum = kcum;
+            a.n = n;
+            a.acc = acc;
+            a.err = h->d_err;
+            char *bw = w + L.total;
+            ba.bin_count = reinterpret_cast<unsigned long long *>(bw + B.count_off);
+            ba.chunk_pre = reinterpret_cast<uint64_t *>(bw + B.pre_off);
+            ba.records = reinterpret_cast<uint64_t *>(bw + B.rec_off);
+            ba.cap = B.cap;
+            ba.nb = B.nb;
+            ba.shift = B.shift;
+            {
+                StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, binned_launches());
+                RAMBO_TRY(launch_binned(ba, g, h->sm_count, s));
+            }
+            ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
+                         h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
+                         h->tune.expand_filter};
+            StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
+            RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
+            return RAMBO_OK;
+        }
+    }
+    if (h->tune.query_path >= 1 && fused_supported(g)) {
         // persistent fused query: length-bucketed queues, probe + expand in one launch
         ProbeArgs a{};
         a.index = h->d_index;
@@ -505,13 +603,22 @@ int reserve_host_offsets(rambo_t *h, size_t bytes) {
 }
 
 // K-mers per chunk of a host-buffer k-mer batch: about 32 MiB of answers.
+// K-mers per chunk of a host-buffer k-mer batch: about 16 MiB of answers
+// unless the knob says otherwise.  The first chunk is a quarter of that, so
+// the copy-out engine starts early.
 uint64_t host_chunk(const rambo_t *h, uint64_t n) {
     uint64_t c = h->tune.host_chunk_kmers;
     if (!c) {
-        c = (32ull << 20) / ((uint64_t)h->g.W * 4 + 8);
+        c = (16ull << 20) / ((uint64_t)h->g.W * 4 + 8);
         if (c < (1u << 14)) c = 1u << 14;
     }
     return c < n ? c : n;
+}
+uint64_t host_chunk_begin(uint64_t c, uint64_t ck, uint64_t n) {
+    if (c == 0) return 0;
+    const uint64_t first = ck >= 4 ? ck / 4 : ck;
+    const uint64_t b = first + (c - 1) * ck;
+    return b < n ? b : n;
 }
 
 // Host-buffer mixed batch.  The sequence branch (copy in, query, copy out)
@@ -525,8 +632,10 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
     const Geometry &g = h->g;
     const uint64_t row = (uint64_t)g.W * 4;
     const uint64_t ck = nk ? host_chunk(h, nk) : 0;
-    const uint64_t nchunks = nk ? (nk + ck - 1) / ck : 0;
-    const int slots = nchunks > 1 ? 2 : (int)nchunks;
+    uint64_t nchunks = 0;
+    while (nk && host_chunk_begin(nchunks, ck, nk) < nk) ++nchunks;
+    const uint32_t want_slots = h->tune.host_slots ? h->tune.host_slots : 3;
+    const int slots = (int)(nchunks < want_slots ? nchunks : want_slots);
     const size_t kin = align_up(ck * 8), kout = align_up(ck * row);
     const size_t kslot = kin + kout + kmers_ws(g, ck);
     uint64_t b_lo = 0, nbytes = 0;
@@ -537,7 +646,7 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
         p_sz = align_up(nbytes + 16);
         o_sz = align_up((ns + 1) * 8);
         s_out = align_up(ns * row);
-        s_ws = seq_ws(g, ns).total;
+        s_ws = seq_ws_for(h, ns, nbytes + 16);
     }
     const size_t seq_bytes = p_sz + o_sz + s_out + s_ws;
     int rc = reserve_stage(h, seq_bytes + (size_t)slots * kslot);
@@ -553,6 +662,7 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
         return code;
     };
     // branch_priority 1: sequences on a high-priority stream; 2: k-mer chunks
+    // (chunk c uses slot c mod slots: its stream and its staging)
     cudaStream_t ss = h->tune.branch_priority == 1 ? h->pstream[0] : h->stream;
     cudaStream_t *ks = h->tune.branch_priority == 2 ? h->pstream : h->kstream;
     cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
@@ -569,17 +679,18 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
             e = cudaMemcpyAsync(d_o, h->h_offs, (ns + 1) * 8, cudaMemcpyHostToDevice, ss);
         if (e != cudaSuccess) return bail(cuda_rc(e));
         rc = query_seqs_enqueue(h, ns, d_p, nbytes + 16, d_o, d_o + 1, d_out,
-                                base + p_sz + o_sz + s_out, ss);
+                                base + p_sz + o_sz + s_out, s_ws, ss);
         if (rc) return bail(rc);
         e = cudaMemcpyAsync(out_s, d_out, ns * row, cudaMemcpyDeviceToHost, ss);
         if (e != cudaSuccess) return bail(cuda_rc(e));
     }
     for (uint64_t c = 0; c < nchunks; ++c) {
-        const int sl = (int)(c & 1);
+        const int sl = (int)(c % (uint64_t)slots);
         cudaStream_t s = ks[sl];
-        if (c < 2 && (e = cudaStreamWaitEvent(s, h->ev_fork, 0)) != cudaSuccess) return bail(cuda_rc(e));
+        if (c < (uint64_t)slots && (e = cudaStreamWaitEvent(s, h->ev_fork, 0)) != cudaSuccess)
+            return bail(cuda_rc(e));
         char *slot = base + seq_bytes + (size_t)sl * kslot;
-        const uint64_t i0 = c * ck, cn = ck < nk - i0 ? ck : nk - i0;
+        const uint64_t i0 = host_chunk_begin(c, ck, nk), cn = host_chunk_begin(c + 1, ck, nk) - i0;
         uint64_t *d_k = reinterpret_cast<uint64_t *>(slot);
         uint32_t *d_out = reinterpret_cast<uint32_t *>(slot + kin);
         e = cudaMemcpyAsync(d_k, kmers + i0, cn * 8, cudaMemcpyHostToDevice, s);
@@ -672,6 +783,8 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.kmer_probe_ctas_per_sm = 0;
     h->tune.host_chunk_kmers = 0;
     h->tune.branch_priority = 0;
+    h->tune.host_slots = 3;
+    h->tune.bin_region_kib = 32768;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -735,6 +848,9 @@ size_t rambo_query_kmers_workspace(const rambo_t *h, uint64_t n) {
 size_t rambo_query_seqs_workspace(const rambo_t *h, uint64_t n) {
     return h ? seq_ws(h->g, n).total : 0;
 }
+size_t rambo_query_seqs_workspace_for(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
+    return h ? seq_ws_for(h, n, packed_bytes) : 0;
+}
 
 // ----------------------------------------------------------------- device
 
@@ -776,7 +892,7 @@ int rambo_query_seqs_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
     return query_seqs_enqueue(h, n, packed, packed_bytes, base_offsets, base_offsets + 1, out,
-                              workspace, static_cast<cudaStream_t>(stream));
+                              workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
 }
 
 int rambo_query_ranges_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
@@ -790,12 +906,14 @@ int rambo_query_ranges_dev(rambo_t *h, uint64_t n, const uint8_t *packed, uint64
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
     return query_seqs_enqueue(h, n, packed, packed_bytes, begins, ends, out, workspace,
-                              static_cast<cudaStream_t>(stream));
+                              workspace_bytes, static_cast<cudaStream_t>(stream));
 }
 
-size_t rambo_query_batch_workspace(const rambo_t *h, uint64_t n_kmers, uint64_t n_seqs) {
+size_t rambo_query_batch_workspace(const rambo_t *h, uint64_t n_kmers, uint64_t n_seqs,
+                                   uint64_t packed_bytes) {
     if (!h) return 0;
-    return (n_kmers ? kmers_ws(h->g, n_kmers) : 0) + (n_seqs ? seq_ws(h->g, n_seqs).total : 0);
+    return (n_kmers ? kmers_ws(h->g, n_kmers) : 0) +
+           (n_seqs ? seq_ws_for(h, n_seqs, packed_bytes + 8) : 0);
 }
 
 int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, uint32_t *out_kmers,
@@ -806,7 +924,8 @@ int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, u
     if (n_kmers == 0 && n_seqs == 0) return RAMBO_OK;
     if ((n_kmers && (!kmers || !out_kmers)) ||
         (n_seqs && (n_seqs >= 0xffffffffULL || !base_offsets || !out_seqs || (!packed && packed_bytes))) ||
-        !workspace || workspace_bytes < rambo_query_batch_workspace(h, n_kmers, n_seqs) ||
+        !workspace || workspace_bytes < (n_kmers ? kmers_ws(h->g, n_kmers) : 0) +
+                                            (n_seqs ? seq_ws(h->g, n_seqs).total : 0) ||
         (reinterpret_cast<uintptr_t>(workspace) & 255))
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
@@ -817,7 +936,7 @@ int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, u
     char *wseq = w + (n_kmers ? kmers_ws(h->g, n_kmers) : 0);
     if (!n_kmers)
         return query_seqs_enqueue(h, n_seqs, packed, packed_bytes, base_offsets, base_offsets + 1,
-                                  out_seqs, wseq, s);
+                                  out_seqs, wseq, workspace_bytes - (size_t)(wseq - w), s);
     // fork the k-mer branch onto a stream of the handle and join it back, so
     // that both branches run at once (also inside a stream capture);
     // branch_priority 1 moves the sequence branch to a high-priority stream
@@ -830,7 +949,7 @@ int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, u
     if (ss != s) RAMBO_TRY(cudaStreamWaitEvent(ss, h->ev_fork, 0));
     const int rk = query_kmers_enqueue(h, n_kmers, kmers, out_kmers, w, sk);
     const int rs = query_seqs_enqueue(h, n_seqs, packed, packed_bytes, base_offsets, base_offsets + 1,
-                                      out_seqs, wseq, ss);
+                                      out_seqs, wseq, workspace_bytes - (size_t)(wseq - w), ss);
     RAMBO_TRY(cudaEventRecord(h->ev_join, sk));
     RAMBO_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
     if (ss != s) {
@@ -1090,11 +1209,12 @@ int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out) {
 int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
     if (!h || !t) return RAMBO_EINVAL;
     if (t->probe_ctas_per_sm > 32 || t->expand_ctas_per_sm == 0 || t->expand_ctas_per_sm > 64 ||
-        t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 1 || t->fused_tile_kmers == 0 ||
+        t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 2 || t->fused_tile_kmers == 0 ||
         t->fused_tile_kmers > (1u << 24) || t->fused_short_max > (1u << 24) || t->smem_docbits > 1 ||
         t->use_nibble_table > 1 || t->expand_filter > 1 || t->early_exit > 1 ||
         t->early_exit_segment == 0 || (t->early_exit_segment & 127) || t->early_exit_segment > (1u << 24) ||
-        t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2)
+        t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2 ||
+        t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22))
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

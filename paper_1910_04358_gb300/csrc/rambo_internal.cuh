@@ -246,6 +246,13 @@ cudaError_t launch_partition(uint32_t *phi, uint32_t K, uint32_t R, uint32_t B, 
 // Exclusive prefix (n+1 values) of the k-mer counts of items
 // [begins[i], ends[i]); with tile > 0, of the tile counts of the items with
 // more than short_max k-mers (ceil(k-mers / tile); shorter items count 0).
+// Device address of the host range [p, p + bytes) when both its ends lie in
+// page-locked host memory that the current device can address (allocated
+// with cudaHostAlloc / cudaMallocHost or registered, mapped under unified
+// addressing) at consistent device addresses; null otherwise (pageable
+// memory, device memory, or a range that does not look like one buffer).
+void *mapped_host_range(const void *p, uint64_t bytes);
+
 // Kernels one launch_kmer_prefix of n items enqueues.
 int kmer_prefix_launches(uint64_t n);
 cudaError_t launch_kmer_prefix(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
@@ -278,6 +285,22 @@ struct FusedQueues {
     unsigned long long *probed;  // early exit: k-mers actually probed (or null)
 };
 bool fused_supported(const Geometry &g);
+// Region-binned probing of a sequence batch (query path 2, groups of at most
+// 16 bytes): bins of `cap` records each, region = pos >> shift.
+struct BinnedArgs {
+    ProbeArgs p;                    // index, hashing, batch, kcum; acc preset to all ones
+    uint64_t *records;              // nb * cap records (group << 32 | query)
+    unsigned long long *bin_count;  // nb: records offered to each bin
+    uint64_t *chunk_pre;            // nb + 1: prefix of the probe pass's work items
+    uint64_t cap;                   // record slots per bin
+    uint32_t nb, shift;
+};
+bool binned_supported(const Geometry &g);
+// Regions of (at most) region_bytes, a power-of-two number of groups, and at
+// most 4096 of them: returns the bin count, *shift = log2(groups per region).
+uint32_t binned_bins(const Geometry &g, uint64_t region_bytes, uint32_t *shift);
+int binned_launches();
+cudaError_t launch_binned(const BinnedArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 // p.acc is unused (the bucket masks of long queries are e.acc).
 cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry &g,
                          const FusedQueues &qs, int grid_override, int sm_count, cudaStream_t s);

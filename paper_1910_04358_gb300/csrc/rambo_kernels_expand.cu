@@ -300,6 +300,17 @@ __global__ void k_build_bytetab(const uint32_t *docbits, uint32_t B, uint32_t R,
     }
 }
 
+// Grid of the table-staging expansions: one resident wave at most, and no
+// more blocks than give each about 512 queries (every block stages the whole
+// table, so small batches would otherwise spend their time staging).
+int nib_grid(int occ, int sm_count, int max_blocks, uint64_t n) {
+    uint64_t g = (uint64_t)(occ > 0 ? occ : 1) * (uint64_t)sm_count;
+    if (g > (uint64_t)max_blocks) g = (uint64_t)max_blocks;
+    const uint64_t by_n = (n + 511) / 512;
+    if (g > by_n) g = by_n;
+    return g > 0 ? (int)g : 1;
+}
+
 }  // namespace
 
 cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cudaStream_t s) {
@@ -343,9 +354,9 @@ cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cud
         if (e2 == cudaSuccess)                                                                     \
             e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expand_nib32<P>,            \
                                                                EXPAND_THREADS, nib32_bytes);       \
-        const int grid = occ * sm_count < max_blocks ? occ * sm_count : max_blocks;                \
+        const int grid = nib_grid(occ, sm_count, max_blocks, a.n);                                  \
         if (e2 == cudaSuccess)                                                                     \
-            k_expand_nib32<P><<<grid > 0 ? grid : 1, EXPAND_THREADS, nib32_bytes, s>>>(a);          \
+            k_expand_nib32<P><<<grid, EXPAND_THREADS, nib32_bytes, s>>>(a);                         \
     }
         RGPU_NIB32(1)
         RGPU_NIB32(2)
@@ -378,8 +389,8 @@ cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cud
         if (e2 == cudaSuccess)                                                                     \
             e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expand_nib<L, V>,           \
                                                                EXPAND_THREADS, nib_bytes);         \
-        const int grid = occ * sm_count < max_blocks ? occ * sm_count : max_blocks;                \
-        if (e2 == cudaSuccess) k_expand_nib<L, V><<<grid > 0 ? grid : 1, EXPAND_THREADS, nib_bytes, s>>>(a); \
+        const int grid = nib_grid(occ, sm_count, max_blocks, a.n);                                  \
+        if (e2 == cudaSuccess) k_expand_nib<L, V><<<grid, EXPAND_THREADS, nib_bytes, s>>>(a);       \
     }
         RGPU_NIB(1, 1)
         RGPU_NIB(1, 2)

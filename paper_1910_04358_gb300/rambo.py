@@ -86,7 +86,9 @@ def load():
             "rambo_query_words_workspace": (sz, [p, u64]),
             "rambo_query_words_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
             "rambo_query_batch": (i, [p, u64, p, p, u64, p, p, p]),
-            "rambo_query_batch_workspace": (sz, [p, u64, u64]),
+            "rambo_probe_host_write": (i, [p, p, u64, u32, p]),
+            "rambo_query_batch_workspace": (sz, [p, u64, u64, u64]),
+            "rambo_query_seqs_workspace_for": (sz, [p, u64, u64]),
             "rambo_query_batch_dev": (i, [p, u64, p, p, u64, p, u64, p, p, p, sz, p]),
         }
         for name, (res, args) in sig.items():
@@ -167,7 +169,8 @@ TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_p
                  "use_byte_table", "byte_table_max_mb", "query_path", "fused_tile_kmers",
                  "fused_short_max", "smem_docbits", "use_nibble_table",
                  "expand_filter", "early_exit", "early_exit_segment",
-                 "kmer_probe_ctas_per_sm", "host_chunk_kmers", "branch_priority")
+                 "kmer_probe_ctas_per_sm", "host_chunk_kmers", "branch_priority",
+                 "host_slots", "bin_region_kib")
 
 
 class _Tuning(C.Structure):
@@ -184,6 +187,13 @@ def probe_gather(buf, record_bytes: int, n_probes: int, variant: int = 0, seed: 
                                      unroll, seed, sink.data_ptr(), _stream_handle(stream)),
            "rambo_probe_gather")
     return sink
+
+
+def probe_host_write(src, dst_pinned, blocks_per_sm: int = 4, stream=None):
+    """SM-driven copy of a CUDA tensor into a page-locked CPU tensor (measurement support)."""
+    _check(load().rambo_probe_host_write(src.data_ptr(), dst_pinned.data_ptr(),
+                                         src.numel() * src.element_size(), blocks_per_sm,
+                                         _stream_handle(stream)), "rambo_probe_host_write")
 
 
 def set_l2_fetch_granularity(nbytes: int) -> int:
@@ -292,7 +302,11 @@ class Index:
             ws = self._ws[stream_key] = Workspace(f"cuda:{self.device}")
         return ws.get(nbytes)
 
-    def workspace_bytes(self, kind: str, n: int) -> int:
+    def workspace_bytes(self, kind: str, n: int, packed_bytes: int | None = None) -> int:
+        """Device workspace of a call; for "seqs" with packed_bytes, the size
+        that lets the tuned query path run (region-binned records included)."""
+        if kind == "seqs" and packed_bytes is not None:
+            return int(load().rambo_query_seqs_workspace_for(self._h, n, packed_bytes))
         f = {"insert": "rambo_insert_workspace", "kmers": "rambo_query_kmers_workspace",
              "seqs": "rambo_query_seqs_workspace"}[kind]
         return int(getattr(load(), f)(self._h, n))
@@ -326,7 +340,7 @@ class Index:
         n = offsets.numel() - 1
         if out is None:
             out = torch.empty((max(n, 0), self.W), dtype=torch.int32, device=offsets.device)
-        need = self.workspace_bytes("seqs", max(n, 0))
+        need = self.workspace_bytes("seqs", max(n, 0), packed.numel())
         s = _stream_handle(stream)
         wp, wn = workspace if workspace is not None else self._workspace(s, need)
         _check(load().rambo_query_seqs_dev(self._h, max(n, 0), _t_ptr(packed), packed.numel(),
@@ -347,7 +361,8 @@ class Index:
             out_kmers = torch.empty((nk, self.W), dtype=torch.int32, device=dev)
         if out_seqs is None:
             out_seqs = torch.empty((ns, self.W), dtype=torch.int32, device=dev)
-        need = int(load().rambo_query_batch_workspace(self._h, nk, ns))
+        pb = packed.numel() if ns and packed is not None else 0
+        need = int(load().rambo_query_batch_workspace(self._h, nk, ns, pb))
         s = _stream_handle(stream)
         wp, wn = workspace if workspace is not None else self._workspace(s, need)
         _check(load().rambo_query_batch_dev(
@@ -364,7 +379,7 @@ class Index:
         n = begins.numel()
         if out is None:
             out = torch.empty((n, self.W), dtype=torch.int32, device=begins.device)
-        need = self.workspace_bytes("seqs", n)
+        need = self.workspace_bytes("seqs", n, packed.numel())
         s = _stream_handle(stream)
         wp, wn = workspace if workspace is not None else self._workspace(s, need)
         _check(load().rambo_query_ranges_dev(self._h, n, _t_ptr(packed), packed.numel(),

@@ -147,7 +147,7 @@ SWEEP = [
 ]
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 @pytest.mark.parametrize("K,B,R,m,eta,k", SWEEP)
 def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k, path):
     p = synth.Params(K=K, B=B, R=R, m=m, eta=eta, k=k, seed=K + B)
@@ -157,7 +157,8 @@ def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k, path):
     o = oracle_index(p, corpus)
     idx = gpu_index(rambo_lib, p, corpus, chunks=3)
     # path 1 (persistent fused launch) with small tiles so long queries span tiles
-    idx.set_tuning(query_path=path, fused_tile_kmers=64, fused_short_max=40)
+    # path 2 (region-binned) with 1 KiB regions so the batch spans many bins
+    idx.set_tuning(query_path=path, fused_tile_kmers=64, fused_short_max=40, bin_region_kib=1)
     assert_index_equal(idx, o, p)
     assert_docbits_equal(idx, o, p)
     assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets),
@@ -188,7 +189,9 @@ def test_tuning_knobs_do_not_change_results(rambo_lib):
                 dict(query_path=0, smem_docbits=1, expand_ctas_per_sm=1),
                 dict(query_path=1, smem_docbits=0, use_byte_table=0),
                 dict(query_path=0, use_nibble_table=1, expand_ctas_per_sm=1),
-                dict(query_path=0, use_nibble_table=0)]
+                dict(query_path=0, use_nibble_table=0),
+                dict(query_path=2, bin_region_kib=0),
+                dict(query_path=2, bin_region_kib=4)]
     for st in settings:
         idx.set_tuning(**st)
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want_s), st
@@ -341,9 +344,59 @@ def test_sequence_batch_past_single_block_scan(rambo_lib):
     o = oracle_index(p, corpus)
     want = o.query_seqs(q.packed, q.offsets)
     idx = gpu_index(rambo_lib, p, corpus)
-    for path in (0, 1):
+    for path in (0, 1, 2):
         idx.set_tuning(query_path=path)
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want), path
+
+
+# ------------------------------------------------ region-binned probing (path 2)
+
+@pytest.mark.parametrize("K,B,R,m,region_kib", [
+    (200, 20, 3, 1 << 16, 64),          # 8-byte groups, 8 regions
+    (300, 32, 4, 1 << 18, 256),         # 16-byte groups, 16 regions
+    (64, 8, 2, (1 << 15) + 123, 16),    # 4-byte groups, m not a power of two, ragged last region
+    (300, 32, 4, 1 << 18, 0),           # default region size: one region
+    (150, 40, 4, 1 << 16, 64),          # 32-byte groups: path 2 unsupported, path 1 runs
+])
+def test_binned_path_matches_oracle(rambo_lib, K, B, R, m, region_kib):
+    torch = _torch()
+    p = synth.Params(K=K, B=B, R=R, m=m, eta=2, k=31, seed=9)
+    rng = np.random.default_rng(K + B)
+    corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=1500, sub_rate=0.01)
+    q = synth.sample_queries(rng, corpus, rng.integers(0, 900, size=300), 0.5)
+    o = oracle_index(p, corpus)
+    want = o.query_seqs(q.packed, q.offsets)
+    idx = gpu_index(rambo_lib, p, corpus)
+    idx.set_tuning(query_path=2, bin_region_kib=region_kib)
+    assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want)
+    assert np.array_equal(idx.query_seqs(q.packed, q.offsets), want)
+    # a workspace without room for the records: the call takes path 1
+    d_p, d_o = _dev(q.packed, np.uint8), _dev(q.offsets.astype(np.uint64), np.int64)
+    small = idx.workspace_bytes("seqs", q.n)
+    buf = torch.empty(small + 256, dtype=torch.uint8, device="cuda")
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    out = idx.query_seqs_dev(d_p, d_o, workspace=(ptr, small))
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(out), want)
+
+
+def test_binned_path_overflow_probes_directly(rambo_lib):
+    # 2,000 queries over the same 1,500 bases: ten times more probe records
+    # than the packed bytes bound the bins for, so most are probed on the spot
+    p = synth.Params(K=100, B=16, R=3, m=1 << 16, eta=2, k=31, seed=3)
+    rng = np.random.default_rng(77)
+    corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=1500, sub_rate=0.01)
+    o = oracle_index(p, corpus)
+    b0, b1 = int(corpus.offsets[7]), int(corpus.offsets[8])
+    one = o.query_seqs(corpus.packed, np.array([b0, b1], dtype=np.uint64))
+    n = 2000
+    idx = gpu_index(rambo_lib, p, corpus)
+    idx.set_tuning(query_path=2, bin_region_kib=64)
+    begins = _dev(np.full(n, b0, dtype=np.uint64), np.int64)
+    ends = _dev(np.full(n, b1, dtype=np.uint64), np.int64)
+    out = idx.query_ranges_dev(_dev(corpus.packed, np.uint8), begins, ends)
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(out), np.repeat(one, n, axis=0))
 
 
 # ------------------------------------------------ mixed batches (both kinds)
@@ -364,13 +417,19 @@ def test_query_batch_host_pipelined_chunks_match_oracle(rambo_lib):
     want_s = o.query_seqs(q.packed, q.offsets)
     idx = gpu_index(rambo_lib, p, corpus)
     for chunk in (0, 1000, 7_001, 3):  # auto, ragged last chunk, one chunk, many
-        for path in (0, 1):
+        for path in (0, 1, 2):
             for prio in (0, 1, 2):
                 idx.set_tuning(host_chunk_kmers=chunk, query_path=path, branch_priority=prio)
                 got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets)
                 assert np.array_equal(got_k, want_k), (chunk, path, prio)
                 assert np.array_equal(got_s, want_s), (chunk, path, prio)
     idx.set_tuning(branch_priority=0)
+    for slots in (1, 2, 4):
+        idx.set_tuning(host_chunk_kmers=1000, host_slots=slots)
+        got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets)
+        assert np.array_equal(got_k, want_k), slots
+        assert np.array_equal(got_s, want_s), slots
+    idx.set_tuning(host_slots=3)
     # either part may be empty; the single-kind calls go through the same path
     idx.set_tuning(host_chunk_kmers=1000)
     got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets[:1])
@@ -402,7 +461,7 @@ def test_query_batch_dev_and_graph_capture_match_oracle(rambo_lib):
     idx = gpu_index(rambo_lib, p, corpus)
     d_k, d_p = _dev(kmers, np.int64), _dev(q.packed, np.uint8)
     d_o = _dev(q.offsets.astype(np.uint64), np.int64)
-    for path in (0, 1):
+    for path in (0, 1, 2):
         for prio in (0, 1, 2):
             idx.set_tuning(query_path=path, branch_priority=prio)
             ok, os_ = idx.query_batch_dev(d_k, d_p, d_o)
@@ -410,8 +469,8 @@ def test_query_batch_dev_and_graph_capture_match_oracle(rambo_lib):
             assert np.array_equal(rambo_lib.as_u32(ok), want_k), (path, prio)
             assert np.array_equal(rambo_lib.as_u32(os_), want_s), (path, prio)
     # captured once, replayed twice into zeroed outputs
-    for prio in (0, 1, 2):
-        idx.set_tuning(branch_priority=prio)
+    for path, prio in ((1, 0), (1, 1), (1, 2), (2, 0)):
+        idx.set_tuning(query_path=path, branch_priority=prio)
         out_k = torch.zeros((kmers.size, idx.W), dtype=torch.int32, device="cuda")
         out_s = torch.zeros((q.n, idx.W), dtype=torch.int32, device="cuda")
         idx.query_batch_dev(d_k, d_p, d_o, out_kmers=out_k, out_seqs=out_s)
