@@ -343,6 +343,13 @@ typedef struct {
     uint32_t bin_region_kib;           /* path 2: index bytes per region (KiB; 0 =     */
                                        /* 32768); regions hold a power-of-two number   */
                                        /* of groups and are at most 4096              */
+    uint32_t bin_rows;                 /* path 2: rows of 32 records a warp probes per */
+                                       /* work item (1, 2, 4 or 8; 0 = 2)              */
+    uint32_t host_direct;              /* host-buffer calls: 1 (default) = kernels     */
+                                       /* write answers straight into output buffers   */
+                                       /* that are page-locked and device-addressable  */
+                                       /* (each must be one such allocation); others   */
+                                       /* are staged and copied as with 0              */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

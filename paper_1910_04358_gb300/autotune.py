@@ -30,6 +30,8 @@ KNOBS = (
     ("expand_ctas_per_sm", (2, 4, 8, 16, 32)),
     ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
     ("kmer_probe_ctas_per_sm", (0, 1, 2, 3, 4)),
+    ("bin_region_kib", (16384, 32768, 65536)),
+    ("bin_rows", (1, 2, 4, 8)),
     ("fused_tile_kmers", (256, 512, 1024, 2048, 4096)),
     ("fused_short_max", (64, 256, 1024, 4096)),
     ("probe_min_kmers_per_warp", (0, 256, 1024, 4096)),
@@ -75,6 +77,8 @@ def autotune(idx, run, outputs, reps: int = 7, knobs=KNOBS, verbose: bool = Fals
             cand = dict(best_cfg)
             cand[knob] = v
             if knob in ("fused_tile_kmers", "fused_short_max") and cand["query_path"] != 1:
+                continue
+            if knob in ("bin_region_kib", "bin_rows") and cand["query_path"] != 2:
                 continue
             idx.set_tuning(**cand)
             ms = _time(run, reps)

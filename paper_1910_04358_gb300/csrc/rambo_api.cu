@@ -359,6 +359,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
             ba.cap = B.cap;
             ba.nb = B.nb;
             ba.shift = B.shift;
+            ba.rows = h->tune.bin_rows ? h->tune.bin_rows : 2;
             {
                 StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, binned_launches());
                 RAMBO_TRY(launch_binned(ba, g, h->sm_count, s));
@@ -665,6 +666,13 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
     // (chunk c uses slot c mod slots: its stream and its staging)
     cudaStream_t ss = h->tune.branch_priority == 1 ? h->pstream[0] : h->stream;
     cudaStream_t *ks = h->tune.branch_priority == 2 ? h->pstream : h->kstream;
+    // host_direct: answers written by the kernels straight into page-locked
+    // output buffers (device-addressable), instead of staged and copied
+    uint32_t *direct_k = nullptr, *direct_s = nullptr;
+    if (h->tune.host_direct) {
+        if (nk) direct_k = static_cast<uint32_t *>(mapped_host_range(out_k, nk * row));
+        if (ns) direct_s = static_cast<uint32_t *>(mapped_host_range(out_s, ns * row));
+    }
     cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
     if (e != cudaSuccess) return bail(cuda_rc(e));
     if (ns && ss != h->stream && (e = cudaStreamWaitEvent(ss, h->ev_fork, 0)) != cudaSuccess)
@@ -672,7 +680,7 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
     if (ns) {
         uint8_t *d_p = reinterpret_cast<uint8_t *>(base);
         uint64_t *d_o = reinterpret_cast<uint64_t *>(base + p_sz);
-        uint32_t *d_out = reinterpret_cast<uint32_t *>(base + p_sz + o_sz);
+        uint32_t *d_out = direct_s ? direct_s : reinterpret_cast<uint32_t *>(base + p_sz + o_sz);
         e = cudaMemcpyAsync(d_p, packed + b_lo, nbytes, cudaMemcpyHostToDevice, ss);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_p + nbytes, 0, 16, ss);
         if (e == cudaSuccess)
@@ -681,8 +689,10 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
         rc = query_seqs_enqueue(h, ns, d_p, nbytes + 16, d_o, d_o + 1, d_out,
                                 base + p_sz + o_sz + s_out, s_ws, ss);
         if (rc) return bail(rc);
-        e = cudaMemcpyAsync(out_s, d_out, ns * row, cudaMemcpyDeviceToHost, ss);
-        if (e != cudaSuccess) return bail(cuda_rc(e));
+        if (!direct_s) {
+            e = cudaMemcpyAsync(out_s, d_out, ns * row, cudaMemcpyDeviceToHost, ss);
+            if (e != cudaSuccess) return bail(cuda_rc(e));
+        }
     }
     for (uint64_t c = 0; c < nchunks; ++c) {
         const int sl = (int)(c % (uint64_t)slots);
@@ -692,13 +702,15 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
         char *slot = base + seq_bytes + (size_t)sl * kslot;
         const uint64_t i0 = host_chunk_begin(c, ck, nk), cn = host_chunk_begin(c + 1, ck, nk) - i0;
         uint64_t *d_k = reinterpret_cast<uint64_t *>(slot);
-        uint32_t *d_out = reinterpret_cast<uint32_t *>(slot + kin);
+        uint32_t *d_out = direct_k ? direct_k + i0 * g.W : reinterpret_cast<uint32_t *>(slot + kin);
         e = cudaMemcpyAsync(d_k, kmers + i0, cn * 8, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return bail(cuda_rc(e));
         rc = query_kmers_enqueue(h, cn, d_k, d_out, slot + kin + kout, s);
         if (rc) return bail(rc);
-        e = cudaMemcpyAsync(out_k + i0 * g.W, d_out, cn * row, cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) return bail(cuda_rc(e));
+        if (!direct_k) {
+            e = cudaMemcpyAsync(out_k + i0 * g.W, d_out, cn * row, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return bail(cuda_rc(e));
+        }
     }
     RAMBO_TRY(sync_own_streams(h));
     return read_and_clear_err(h);
@@ -785,6 +797,8 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.branch_priority = 0;
     h->tune.host_slots = 3;
     h->tune.bin_region_kib = 32768;
+    h->tune.bin_rows = 2;
+    h->tune.host_direct = 1;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -1214,7 +1228,9 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         t->use_nibble_table > 1 || t->expand_filter > 1 || t->early_exit > 1 ||
         t->early_exit_segment == 0 || (t->early_exit_segment & 127) || t->early_exit_segment > (1u << 24) ||
         t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2 ||
-        t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22))
+        t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22) ||
+        (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
+        t->host_direct > 1)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

@@ -294,6 +294,7 @@ struct BinnedArgs {
     uint64_t *chunk_pre;            // nb + 1: prefix of the probe pass's work items
     uint64_t cap;                   // record slots per bin
     uint32_t nb, shift;
+    uint32_t rows;                  // probe pass: rows of 32 records per work item (1, 2, 4, 8)
 };
 bool binned_supported(const Geometry &g);
 // Regions of (at most) region_bytes, a power-of-two number of groups, and at

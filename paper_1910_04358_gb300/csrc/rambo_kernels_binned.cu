@@ -8,10 +8,10 @@
 // region (a power-of-two number of groups spanning about 32 MiB):
 //   scatter  every k-mer is extracted and hashed once; each probe becomes a
 //            record (group, query) in its region's bin.  A block stages a
-//            tile of records, sorts them by bin in shared memory and writes
-//            each bin's run with one reservation (atomicAdd on the bin's
-//            counter).  A record that finds its bin's share of the workspace
-//            full is probed on the spot instead.
+//            tile of records with their ranks in a shared-memory histogram,
+//            reserves each bin's run with one atomicAdd on the bin's counter
+//            and writes every record to its slot.  A record that finds its
+//            bin's share of the workspace full is probed on the spot.
 //   chunks   one block turns the bin counts into a prefix of work items.
 //   probe    warps take the work items in region order, so at any moment the
 //            grid probes inside one or two regions that fit in L2 and each
@@ -27,8 +27,6 @@ namespace {
 
 constexpr int BIN_THREADS = 256;
 constexpr uint32_t BIN_TILE_RECS = 2048;  // probe records staged per block tile
-constexpr uint32_t BIN_CHUNK = 256;       // records per warp work item of the probe pass
-constexpr int BIN_U = BIN_CHUNK / 32;     // records per lane per work item
 constexpr uint64_t BIN_MAX = 4096;        // most bins (index regions) per batch
 
 __device__ __forceinline__ uint64_t make_rec(uint32_t pos, uint32_t q) {
@@ -81,93 +79,99 @@ __device__ uint64_t block_excl_scan(const TI *in, uint64_t *out, uint32_t n) {
 template <int SW>
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(BinnedArgs a) {
     extern __shared__ uint64_t smem64[];
-    uint64_t *s_rec = smem64;                        // BIN_TILE_RECS, tile order
-    uint64_t *s_sorted = s_rec + BIN_TILE_RECS;      // BIN_TILE_RECS, bin order
-    uint64_t *s_pre = s_sorted + BIN_TILE_RECS;      // nb: tile-local exclusive prefix
-    uint64_t *s_base = s_pre + a.nb;                 // nb: first slot of the tile's run
+    uint64_t *s_rec = smem64;                                        // BIN_TILE_RECS, tile order
+    uint64_t *s_base = s_rec + BIN_TILE_RECS;                        // nb: first slot of the tile's run
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_base + a.nb);  // nb: records per bin
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_hist + a.nb);  // BIN_TILE_RECS
-    __shared__ uint64_t s_q[2];
+    __shared__ uint64_t s_qa[BIN_THREADS], s_qb[BIN_THREADS];
 
     const ProbeArgs &p = a.p;
     const uint64_t T = p.kcum[p.n];
     const uint32_t kpt = BIN_TILE_RECS / p.eta;  // k-mers per tile
     const uint64_t tiles = (T + kpt - 1) / kpt;
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const uint64_t t0 = tile * kpt;
-        const uint64_t t1 = t0 + kpt < T ? t0 + kpt : T;
-        for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) s_hist[b] = 0;
-        if (threadIdx.x == 0) {
-            s_q[0] = find_query(p.kcum, p.n, t0);
-            s_q[1] = find_query(p.kcum, p.n, t1 - 1);
-        }
-        __syncthreads();
-        const uint64_t qa = s_q[0], qb = s_q[1];
-        // phase 1: k-mers of the tile -> records, tile-local histogram
-        for (uint64_t g = t0 + threadIdx.x; g < t1; g += BIN_THREADS) {
-            uint64_t lo = qa, hi = qb + 1;
-            while (hi - lo > 1) {
-                const uint64_t mid = (lo + hi) >> 1;
-                if (p.kcum[mid] <= g) lo = mid;
-                else hi = mid;
-            }
-            const uint64_t start = p.offsets[lo] + p.base_shift + (g - p.kcum[lo]);
-            const uint64_t c = canonical_from_window(base_window(p.packed, p.packed_bytes, start), p.k);
-            const uint64_t km = mh_mix_key(c);
-            const uint32_t i0 = (uint32_t)(g - t0) * p.eta;
-            for (uint32_t j = 0; j < p.eta; ++j) {
-                const uint32_t pos = reduce_pos(mh_first_word(km, p.seed32 + j), p.m, p.m_pow2);
-                s_rec[i0 + j] = make_rec(pos, (uint32_t)lo);
-                s_rank[i0 + j] = (uint16_t)atomicAdd(&s_hist[pos >> a.shift], 1u);
+    for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) s_hist[b] = 0;
+    // this block's tiles are blockIdx.x + i * gridDim.x; their query ranges
+    // are looked up BIN_THREADS tiles at a time, one tile per thread
+    for (uint64_t i0 = 0; blockIdx.x + i0 * gridDim.x < tiles; i0 += BIN_THREADS) {
+        {
+            const uint64_t tile = blockIdx.x + (i0 + threadIdx.x) * gridDim.x;
+            if (tile < tiles) {
+                const uint64_t t0 = tile * kpt, t1 = t0 + kpt < T ? t0 + kpt : T;
+                s_qa[threadIdx.x] = find_query(p.kcum, p.n, t0);
+                s_qb[threadIdx.x] = find_query(p.kcum, p.n, t1 - 1);
             }
         }
         __syncthreads();
-        // phase 2: tile-local prefix; reserve every bin's run once
-        block_excl_scan(s_hist, s_pre, a.nb);
-        for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) {
-            const uint64_t cnt = s_hist[b];
-            s_base[b] = cnt ? atomicAdd(a.bin_count + b, (unsigned long long)cnt) : 0ull;
-        }
-        __syncthreads();
-        // phase 3: records sorted by bin in shared memory, then written as runs
-        const uint32_t nrec = (uint32_t)(t1 - t0) * p.eta;
-        for (uint32_t i = threadIdx.x; i < nrec; i += BIN_THREADS) {
-            const uint64_t r = s_rec[i];
-            const uint32_t b = (uint32_t)(r >> 32) >> a.shift;
-            s_sorted[s_pre[b] + s_rank[i]] = r;
-        }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < nrec; i += BIN_THREADS) {
-            const uint64_t r = s_sorted[i];
-            const uint32_t pos = (uint32_t)(r >> 32), q = (uint32_t)r;
-            const uint32_t b = pos >> a.shift;
-            const uint64_t slot = s_base[b] + (i - s_pre[b]);
-            if (slot < a.cap) {
-                __stcs(reinterpret_cast<unsigned long long *>(a.records) + (uint64_t)b * a.cap + slot,
-                       (unsigned long long)r);
-            } else {  // the bin's share is full: probe this record now
-                const Slice<SW> v = ld_slice<SW>(p.index + (uint64_t)pos * p.Gw);
-                flush_slice<SW>(p.acc, q, p.Gw, 0, v);
+        for (uint32_t i = 0; i < BIN_THREADS; ++i) {
+            const uint64_t tile = blockIdx.x + (i0 + i) * gridDim.x;
+            if (tile >= tiles) break;
+            const uint64_t t0 = tile * kpt;
+            const uint64_t t1 = t0 + kpt < T ? t0 + kpt : T;
+            const uint64_t qa = s_qa[i], qb = s_qb[i];
+            // phase 1: k-mers of the tile -> records; rank within the bin's run
+            for (uint64_t g = t0 + threadIdx.x; g < t1; g += BIN_THREADS) {
+                uint64_t lo = qa, hi = qb + 1;
+                while (hi - lo > 1) {
+                    const uint64_t mid = (lo + hi) >> 1;
+                    if (p.kcum[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                const uint64_t start = p.offsets[lo] + p.base_shift + (g - p.kcum[lo]);
+                const uint64_t c = canonical_from_window(base_window(p.packed, p.packed_bytes, start), p.k);
+                const uint64_t km = mh_mix_key(c);
+                const uint32_t r0 = (uint32_t)(g - t0) * p.eta;
+                for (uint32_t j = 0; j < p.eta; ++j) {
+                    const uint32_t pos = reduce_pos(mh_first_word(km, p.seed32 + j), p.m, p.m_pow2);
+                    s_rec[r0 + j] = make_rec(pos, (uint32_t)lo);
+                    s_rank[r0 + j] = (uint16_t)atomicAdd(&s_hist[pos >> a.shift], 1u);
+                }
             }
+            __syncthreads();
+            // phase 2: reserve every bin's run once
+            for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) {
+                const uint32_t cnt = s_hist[b];
+                s_base[b] = cnt ? atomicAdd(a.bin_count + b, (unsigned long long)cnt) : 0ull;
+            }
+            __syncthreads();
+            // phase 3: every record to its slot (the bin's share full: probe it now)
+            const uint32_t nrec = (uint32_t)(t1 - t0) * p.eta;
+            for (uint32_t r = threadIdx.x; r < nrec; r += BIN_THREADS) {
+                const uint64_t rec = s_rec[r];
+                const uint32_t pos = (uint32_t)(rec >> 32), q = (uint32_t)rec;
+                const uint32_t b = pos >> a.shift;
+                const uint64_t slot = s_base[b] + s_rank[r];
+                if (slot < a.cap) {
+                    __stcs(reinterpret_cast<unsigned long long *>(a.records) + (uint64_t)b * a.cap + slot,
+                           (unsigned long long)rec);
+                } else {
+                    const Slice<SW> v = ld_slice<SW>(p.index + (uint64_t)pos * p.Gw);
+                    flush_slice<SW>(p.acc, q, p.Gw, 0, v);
+                }
+            }
+            for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) s_hist[b] = 0;
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
 // One block: chunk_pre[b] = exclusive prefix over bins of their work items,
 // chunk_pre[nb] = total.
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_chunks(BinnedArgs a) {
+    const uint32_t chunk = 32u * a.rows;
     for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) {
         const uint64_t cnt = a.bin_count[b] < a.cap ? a.bin_count[b] : a.cap;
-        a.chunk_pre[b] = (cnt + BIN_CHUNK - 1) / BIN_CHUNK;
+        a.chunk_pre[b] = (cnt + chunk - 1) / chunk;
     }
     __syncthreads();
     const uint64_t total = block_excl_scan(a.chunk_pre, a.chunk_pre, a.nb);
     if (threadIdx.x == 0) a.chunk_pre[a.nb] = total;
 }
 
-template <int SW>
+// U rows of 32 records per warp work item; the grid's work items in flight
+// span U * 32 * (warps) records, which should stay within about one region.
+template <int SW, int BIN_U>
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_probe(BinnedArgs a) {
+    constexpr uint32_t BIN_CHUNK = 32u * BIN_U;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (uint64_t)blockIdx.x * (BIN_THREADS / 32) + (threadIdx.x >> 5);
     const uint64_t nwarps = (uint64_t)gridDim.x * (BIN_THREADS / 32);
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin_probe(BinnedArgs a) {
 }
 
 size_t scatter_smem(uint32_t nb) {
-    return (size_t)BIN_TILE_RECS * 8 * 2 + (size_t)nb * (8 + 8 + 4) + (size_t)BIN_TILE_RECS * 2;
+    return (size_t)BIN_TILE_RECS * 8 + (size_t)nb * (8 + 4) + (size_t)BIN_TILE_RECS * 2;
 }
 
 template <int SW>
@@ -236,9 +240,17 @@ cudaError_t launch_binned_t(const BinnedArgs &a, int sm_count, cudaStream_t s) {
     k_bin_scatter<SW><<<(occ > 0 ? occ : 1) * sm_count, BIN_THREADS, smem, s>>>(a);
     k_bin_chunks<<<1, BIN_THREADS, 0, s>>>(a);
     int occ_p = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_bin_probe<SW>, BIN_THREADS, 0);
-    if (e != cudaSuccess) return e;
-    k_bin_probe<SW><<<(occ_p > 0 ? occ_p : 1) * sm_count, BIN_THREADS, 0, s>>>(a);
+#define RGPU_BIN_PROBE(U)                                                                          \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_bin_probe<SW, U>, BIN_THREADS, 0); \
+    if (e != cudaSuccess) return e;                                                                \
+    k_bin_probe<SW, U><<<(occ_p > 0 ? occ_p : 1) * sm_count, BIN_THREADS, 0, s>>>(a);
+    switch (a.rows) {
+        case 1: RGPU_BIN_PROBE(1) break;
+        case 2: RGPU_BIN_PROBE(2) break;
+        case 4: RGPU_BIN_PROBE(4) break;
+        default: RGPU_BIN_PROBE(8) break;
+    }
+#undef RGPU_BIN_PROBE
     return cudaGetLastError();
 }
 

@@ -430,6 +430,21 @@ def test_query_batch_host_pipelined_chunks_match_oracle(rambo_lib):
         assert np.array_equal(got_k, want_k), slots
         assert np.array_equal(got_s, want_s), slots
     idx.set_tuning(host_slots=3)
+    # answers written straight into page-locked outputs (and pageable ones staged)
+    torch = _torch()
+    pin_k = torch.zeros((kmers.size, idx.W), dtype=torch.int32).pin_memory().numpy()
+    pin_s = torch.zeros((q.n, idx.W), dtype=torch.int32).pin_memory().numpy()
+    for direct in (1, 0):
+        for chunk in (0, 1000):
+            idx.set_tuning(host_direct=direct, host_chunk_kmers=chunk)
+            pin_k[:] = 0
+            pin_s[:] = 0
+            idx.query_batch(kmers, q.packed, q.offsets, out_kmers=pin_k, out_seqs=pin_s)
+            assert np.array_equal(pin_k.view(np.uint32), want_k), (direct, chunk)
+            assert np.array_equal(pin_s.view(np.uint32), want_s), (direct, chunk)
+            got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets)  # pageable outputs
+            assert np.array_equal(got_k, want_k) and np.array_equal(got_s, want_s), (direct, chunk)
+    idx.set_tuning(host_direct=0, host_chunk_kmers=0)
     # either part may be empty; the single-kind calls go through the same path
     idx.set_tuning(host_chunk_kmers=1000)
     got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets[:1])
