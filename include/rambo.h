@@ -350,6 +350,11 @@ typedef struct {
                                        /* that are page-locked and device-addressable  */
                                        /* (each must be one such allocation); others   */
                                        /* are staged and copied as with 0              */
+    uint32_t expand_tc;                /* 1: expansion on the tensor cores (an exact   */
+                                       /* 0/1 product of bucket masks and the          */
+                                       /* transposed bucket->document bitmaps) when    */
+                                       /* R*B + 2 <= 256, R <= 15 and the bitmaps fit  */
+                                       /* in shared memory                             */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

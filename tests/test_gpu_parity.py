@@ -191,7 +191,9 @@ def test_tuning_knobs_do_not_change_results(rambo_lib):
                 dict(query_path=0, use_nibble_table=1, expand_ctas_per_sm=1),
                 dict(query_path=0, use_nibble_table=0),
                 dict(query_path=2, bin_region_kib=0),
-                dict(query_path=2, bin_region_kib=4)]
+                dict(query_path=2, bin_region_kib=4),
+                dict(query_path=0, expand_tc=1),
+                dict(query_path=2, expand_tc=1)]
     for st in settings:
         idx.set_tuning(**st)
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want_s), st
@@ -322,7 +324,8 @@ def test_expansion_variants_on_many_kmer_queries(rambo_lib, K, B, R):
     o = oracle_index(p, corpus)
     want = o.query_kmers(kmers, threads=4)
     idx = gpu_index(rambo_lib, p, corpus)
-    for st in (dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=1),
+    for st in (dict(expand_tc=1),
+               dict(expand_tc=0, expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=1),
                dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=0),
                dict(expand_ctas_per_sm=8, use_nibble_table=1, expand_filter=0),
                dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=1),
@@ -332,6 +335,11 @@ def test_expansion_variants_on_many_kmer_queries(rambo_lib, K, B, R):
         got = idx.query_kmers_dev(_dev(kmers, np.int64))
         idx.sync()
         assert np.array_equal(rambo_lib.as_u32(got), want), st
+    # the tensor-core expansion on a batch smaller than one 128-query tile
+    idx.set_tuning(expand_tc=1)
+    got = idx.query_kmers_dev(_dev(kmers[:5], np.int64))
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(got), want[:5])
 
 
 def test_sequence_batch_past_single_block_scan(rambo_lib):
