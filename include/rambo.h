@@ -355,6 +355,11 @@ typedef struct {
                                        /* transposed bucket->document bitmaps) when    */
                                        /* R*B + 2 <= 256, R <= 15 and the bitmaps fit  */
                                        /* in shared memory                             */
+    uint32_t host_fused_ctas_per_sm;   /* host-buffer batches with both kinds: the     */
+                                       /* persistent fused launch takes at most this   */
+                                       /* many CTAs per SM (0 = as probe_ctas_per_sm;  */
+                                       /* default 1), leaving room for the k-mer       */
+                                       /* chunks whose copies out bound the call       */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

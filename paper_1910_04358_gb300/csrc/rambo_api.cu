@@ -314,9 +314,11 @@ Aligned align_packed(const uint8_t *packed, uint64_t packed_bytes) {
 }
 
 // Items are [begins[i], ends[i]); a CSR batch passes (offsets, offsets + 1).
+// fused_ctas_cap > 0 caps the persistent fused launch at that many CTAs per
+// SM (so that other kernels of the same batch can run beside it).
 int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
                        const uint64_t *offsets, const uint64_t *ends, uint32_t *out, void *ws,
-                       size_t ws_bytes, cudaStream_t s) {
+                       size_t ws_bytes, cudaStream_t s, uint32_t fused_ctas_cap = 0) {
     const Geometry &g = h->g;
     const SeqWs L = seq_ws(g, n);
     char *w = static_cast<char *>(ws);
@@ -413,7 +415,9 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
                                          qs.tile, qs.short_max));
         }
         StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 2);
-        const int go = h->tune.probe_ctas_per_sm ? (int)(h->sm_count * h->tune.probe_ctas_per_sm) : 0;
+        uint32_t ctas = h->tune.probe_ctas_per_sm;
+        if (fused_ctas_cap && (ctas == 0 || ctas > fused_ctas_cap)) ctas = fused_ctas_cap;
+        const int go = ctas ? (int)(h->sm_count * ctas) : 0;
         RAMBO_TRY(launch_fused(a, e, g, qs, go, h->sm_count, s));
         return RAMBO_OK;
     }
@@ -694,8 +698,10 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_o, h->h_offs, (ns + 1) * 8, cudaMemcpyHostToDevice, ss);
         if (e != cudaSuccess) return bail(cuda_rc(e));
+        // with k-mer chunks beside it, the fused launch leaves room for them:
+        // their copies out are what bounds a host call
         rc = query_seqs_enqueue(h, ns, d_p, nbytes + 16, d_o, d_o + 1, d_out,
-                                base + p_sz + o_sz + s_out, s_ws, ss);
+                                base + p_sz + o_sz + s_out, s_ws, ss, nk ? h->tune.host_fused_ctas_per_sm : 0u);
         if (rc) return bail(rc);
         if (!direct_s) {
             e = cudaMemcpyAsync(out_s, d_out, ns * row, cudaMemcpyDeviceToHost, ss);
@@ -808,6 +814,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.bin_rows = 2;
     h->tune.host_direct = 1;
     h->tune.expand_tc = 0;
+    h->tune.host_fused_ctas_per_sm = 1;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -1241,7 +1248,7 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2 ||
         t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22) ||
         (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
-        t->host_direct > 1 || t->expand_tc > 1)
+        t->host_direct > 1 || t->expand_tc > 1 || t->host_fused_ctas_per_sm > 32)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

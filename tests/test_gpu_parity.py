@@ -432,6 +432,11 @@ def test_query_batch_host_pipelined_chunks_match_oracle(rambo_lib):
                 assert np.array_equal(got_k, want_k), (chunk, path, prio)
                 assert np.array_equal(got_s, want_s), (chunk, path, prio)
     idx.set_tuning(branch_priority=0)
+    for cap in (0, 2):  # the fused launch's CTA cap beside the k-mer chunks
+        idx.set_tuning(host_fused_ctas_per_sm=cap, query_path=1)
+        got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets)
+        assert np.array_equal(got_k, want_k) and np.array_equal(got_s, want_s), cap
+    idx.set_tuning(host_fused_ctas_per_sm=1)
     for slots in (1, 2, 4):
         idx.set_tuning(host_chunk_kmers=1000, host_slots=slots)
         got_k, got_s = idx.query_batch(kmers, q.packed, q.offsets)
