@@ -345,11 +345,11 @@ typedef struct {
                                        /* of groups and are at most 4096              */
     uint32_t bin_rows;                 /* path 2: rows of 32 records a warp probes per */
                                        /* work item (1, 2, 4 or 8; 0 = 2)              */
-    uint32_t host_direct;              /* host-buffer calls: 1 (default) = kernels     */
-                                       /* write answers straight into output buffers   */
-                                       /* that are page-locked and device-addressable  */
-                                       /* (each must be one such allocation); others   */
-                                       /* are staged and copied as with 0              */
+    uint32_t host_direct;              /* host-buffer calls: 1 = kernels write answers */
+                                       /* straight into output buffers that are        */
+                                       /* page-locked and device-addressable (each     */
+                                       /* must be one such allocation); others are     */
+                                       /* staged and copied as with 0 (the default)    */
     uint32_t expand_tc;                /* 1: expansion on the tensor cores (an exact   */
                                        /* 0/1 product of bucket masks and the          */
                                        /* transposed bucket->document bitmaps) when    */
@@ -389,6 +389,14 @@ int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t record_byte
  * argument is out of range.  Asynchronous on `stream`. */
 int rambo_probe_host_write(const void *src, void *dst_host, uint64_t bytes, uint32_t blocks_per_sm,
                            void *stream);
+
+/* Failure-detection check: enqueues on `stream` one kernel whose thread
+ * waits on an mbarrier that nothing ever completes, with the same bounded
+ * wait the tensor-core expansion uses, here of `spins` polls (1..2^22).  The
+ * wait runs out and latches the error that the next rambo_sync on that
+ * stream reports as RAMBO_ETIMEOUT; nothing faults or hangs, and the handle
+ * stays usable.  RAMBO_EINVAL for spins out of range. */
+int rambo_probe_wait_expiry(rambo_t *h, uint64_t spins, void *stream);
 
 /* Reads (into *previous) and, if bytes > 0, sets the current context's L2
  * fetch granularity limit (32, 64 or 128 bytes).  A per-process context

@@ -812,7 +812,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.host_slots = 3;
     h->tune.bin_region_kib = 32768;
     h->tune.bin_rows = 2;
-    h->tune.host_direct = 1;
+    h->tune.host_direct = 0;
     h->tune.expand_tc = 0;
     h->tune.host_fused_ctas_per_sm = 1;
     if ((rc = apply_bytetab(h))) return fail(rc);
@@ -987,6 +987,13 @@ int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, u
         RAMBO_TRY(cudaStreamWaitEvent(s, h->ev_join2, 0));
     }
     return rk ? rk : rs;
+}
+
+int rambo_probe_wait_expiry(rambo_t *h, uint64_t spins, void *stream) {
+    if (!h || spins == 0 || spins > (1ull << 22)) return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    return cuda_rc(launch_wait_expiry(h->d_err, spins, static_cast<cudaStream_t>(stream)));
 }
 
 int rambo_sync(rambo_t *h, void *stream) {

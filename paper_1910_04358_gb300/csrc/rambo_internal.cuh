@@ -316,6 +316,8 @@ cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cud
 // the launcher needs a.err.
 size_t expand_tc_smem(const ExpandArgs &a);
 cudaError_t launch_expand_tc(const ExpandArgs &a, int sm_count, cudaStream_t s);
+// A bounded mbarrier wait that nothing completes; latches ERR_WAIT on expiry.
+cudaError_t launch_wait_expiry(uint32_t *err, uint64_t spins, cudaStream_t s);
 uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W);
 uint64_t nibtab_words(uint32_t B, uint32_t R, uint32_t W);
 cudaError_t launch_build_nibtab(const uint32_t *docbits, uint32_t B, uint32_t R, uint32_t W,

@@ -110,10 +110,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait for the given phase parity; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint64_t i = 0; i < TC_WAIT_SPINS; ++i)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t spins = TC_WAIT_SPINS) {
+    for (uint64_t i = 0; i < spins; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// A wait that nothing completes: one thread waits on a fresh mbarrier (no
+// arrivals are ever made) with the kernels' bounded wait and latches ERR_WAIT
+// when it gives up.  It exercises the timeout path of the tensor-core
+// expansion without any fault or hang.
+__global__ void k_wait_expiry(uint32_t *err, uint64_t spins) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    if (!mbar_wait(b, 0, spins)) atomicOr(err, ERR_WAIT);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -367,6 +379,11 @@ size_t expand_tc_smem(const ExpandArgs &a) {
     const size_t bytes = 2 * (size_t)TC_M * kdim + (size_t)nch * TC_N * kdim + sizeof(TcShared);
     if (bytes > TC_SMEM_MAX) return 0;
     return bytes < TC_SMEM_MIN ? TC_SMEM_MIN : bytes;
+}
+
+cudaError_t launch_wait_expiry(uint32_t *err, uint64_t spins, cudaStream_t s) {
+    k_wait_expiry<<<1, 32, 0, s>>>(err, spins);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_expand_tc(const ExpandArgs &a, int sm_count, cudaStream_t s) {

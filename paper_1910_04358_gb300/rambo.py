@@ -87,6 +87,7 @@ def load():
             "rambo_query_words_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
             "rambo_query_batch": (i, [p, u64, p, p, u64, p, p, p]),
             "rambo_probe_host_write": (i, [p, p, u64, u32, p]),
+            "rambo_probe_wait_expiry": (i, [p, u64, p]),
             "rambo_query_batch_workspace": (sz, [p, u64, u64, u64]),
             "rambo_query_seqs_workspace_for": (sz, [p, u64, u64]),
             "rambo_query_batch_dev": (i, [p, u64, p, p, u64, p, u64, p, p, p, sz, p]),
@@ -387,6 +388,12 @@ class Index:
                                              _t_ptr(begins), _t_ptr(ends), _t_ptr(out), wp, wn, s),
                "rambo_query_ranges_dev")
         return out
+
+    def probe_wait_expiry(self, spins: int = 1000, stream=None):
+        """Enqueues a bounded wait that runs out (failure-detection check);
+        the next sync() raises RamboError with RAMBO_ETIMEOUT."""
+        _check(load().rambo_probe_wait_expiry(self._h, spins, _stream_handle(stream)),
+               "rambo_probe_wait_expiry")
 
     def sync(self, stream=None):
         _check(load().rambo_sync(self._h, _stream_handle(stream)), "rambo_sync")
