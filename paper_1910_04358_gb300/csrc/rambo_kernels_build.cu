@@ -49,13 +49,16 @@ __device__ __forceinline__ uint64_t kmer_count(const uint64_t *begins, const uin
     const uint64_t L = b1 - b0;
     const uint64_t nk = L >= k ? L - k + 1 : 0;
     if (cm.tile == 0) return nk;
-    return nk > cm.short_max ? (nk + cm.tile - 1) / cm.tile : 0;
+    if (nk <= cm.short_max) return 0;
+    if (nk < (1ull << 31)) return ((uint32_t)nk + cm.tile - 1u) / cm.tile;  // tile < 2^25
+    return (nk + cm.tile - 1) / cm.tile;
 }
 
-// Block-wide exclusive scan of one value per thread; returns the prefix and
-// writes the block total to *total.
+// Block-wide exclusive scan of one value per thread (THREADS a multiple of
+// 32, at most 1024); returns the prefix and writes the block total to *total.
+template <int THREADS = SCAN_THREADS>
 __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *total) {
-    __shared__ uint64_t warp_sums[SCAN_THREADS / 32];
+    __shared__ uint64_t warp_sums[THREADS / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t incl = v;
 #pragma unroll
@@ -66,17 +69,17 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *t
     if (lane == 31) warp_sums[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        uint64_t s = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
+        uint64_t s = lane < THREADS / 32 ? warp_sums[lane] : 0;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint64_t y = __shfl_up_sync(FULL, s, off);
             if (lane >= off) s += y;
         }
-        if (lane < SCAN_THREADS / 32) warp_sums[lane] = s;  // inclusive warp prefix
+        if (lane < THREADS / 32) warp_sums[lane] = s;  // inclusive warp prefix
     }
     __syncthreads();
     const uint64_t before = wid ? warp_sums[wid - 1] : 0;
-    *total = warp_sums[SCAN_THREADS / 32 - 1];
+    *total = warp_sums[THREADS / 32 - 1];
     __syncthreads();
     return before + incl - v;
 }
@@ -126,31 +129,43 @@ k_prefix_final(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_
     }
 }
 
-// Small batches: the whole scan by one block, SCAN_TILE items per pass (one
-// launch instead of three); kcum[n] = grand total.
+// Small batches: the whole scan in one block of 1024 threads (one launch
+// instead of three).  Each pass counts a tile of items with coalesced loads
+// into shared memory, then every thread scans four consecutive counts;
+// kcum[n] = grand total.
 constexpr uint64_t SCAN_SINGLE_MAX = 16 * SCAN_TILE;
+constexpr int SCAN1_THREADS = 1024;
+constexpr int SCAN1_ITEMS = 4;
+constexpr uint32_t SCAN1_TILE = SCAN1_THREADS * SCAN1_ITEMS;
 
-__global__ void __launch_bounds__(SCAN_THREADS)
+__global__ void __launch_bounds__(SCAN1_THREADS)
 k_prefix_single(const uint64_t *begins, const uint64_t *ends, uint64_t n, uint32_t k,
                 uint64_t limit, uint64_t *kcum, uint32_t *err, CountMode cm) {
+    __shared__ uint64_t s_cnt[SCAN1_TILE];
     uint64_t carry = 0;
-    for (uint64_t base = 0; base < n; base += SCAN_TILE) {
-        const uint64_t i0 = base + (uint64_t)threadIdx.x * SCAN_ITEMS;
-        uint64_t c[SCAN_ITEMS];
+    for (uint64_t base = 0; base < n; base += SCAN1_TILE) {
+#pragma unroll
+        for (int j = 0; j < SCAN1_ITEMS; ++j) {
+            const uint32_t t = threadIdx.x + j * SCAN1_THREADS;
+            s_cnt[t] = base + t < n ? kmer_count(begins, ends, base + t, k, limit, err, cm) : 0;
+        }
+        __syncthreads();
+        uint64_t c[SCAN1_ITEMS];
         uint64_t sum = 0;
 #pragma unroll
-        for (int j = 0; j < SCAN_ITEMS; ++j) {
-            c[j] = i0 + j < n ? kmer_count(begins, ends, i0 + j, k, limit, err, cm) : 0;
+        for (int j = 0; j < SCAN1_ITEMS; ++j) {
+            c[j] = s_cnt[threadIdx.x * SCAN1_ITEMS + j];
             sum += c[j];
         }
         uint64_t total;
-        uint64_t run = carry + block_exclusive_scan(sum, &total);
+        uint64_t run = carry + block_exclusive_scan<SCAN1_THREADS>(sum, &total);
+        const uint64_t i0 = base + (uint64_t)threadIdx.x * SCAN1_ITEMS;
 #pragma unroll
-        for (int j = 0; j < SCAN_ITEMS; ++j) {
+        for (int j = 0; j < SCAN1_ITEMS; ++j) {
             if (i0 + j < n) kcum[i0 + j] = run;
             run += c[j];
         }
-        carry += total;
+        carry += total;  // the scan ends with a barrier: s_cnt may be refilled
     }
     if (threadIdx.x == 0) kcum[n] = carry;
 }
@@ -333,7 +348,7 @@ cudaError_t launch_kmer_prefix(const uint64_t *begins, const uint64_t *ends, uin
     if (nblk == 0) return cudaSuccess;
     const CountMode cm{tile, short_max};
     if (n <= SCAN_SINGLE_MAX) {
-        k_prefix_single<<<1, SCAN_THREADS, 0, s>>>(begins, ends, n, k, limit, kcum, err, cm);
+        k_prefix_single<<<1, SCAN1_THREADS, 0, s>>>(begins, ends, n, k, limit, kcum, err, cm);
         return cudaGetLastError();
     }
     k_prefix_partial<<<(unsigned)nblk, SCAN_THREADS, 0, s>>>(begins, ends, n, k, limit, block_sums, err, cm);
