@@ -157,6 +157,22 @@ def probe_bytes_per_kmer(info) -> int:
     return info["eta"] * SECTOR * ((g + SECTOR - 1) // SECTOR)
 
 
+def host_cpu() -> str:
+    """Architecture, core count and model name of the host cores."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{platform.machine()}, {os.cpu_count()} cores" + (f", {model}" if model else "")
+
+
 def effective_path(tuning, info) -> int:
     """Sequence query path the library takes for this tuning and geometry (the
     binding always passes a workspace large enough for path 2)."""
@@ -339,7 +355,8 @@ def run_reference(args):
         "query_bp_per_s": bp * len(times) / total,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{ks.size} k-mers + {so.size - 1} sequences per step "
-                                   f"({units} k-mers), restricted-mode index built in {build_s:.1f} s"},
+                                   f"({units} k-mers), restricted-mode index built in {build_s:.1f} s",
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -693,7 +710,8 @@ def run_ours(args):
                          f"x {reps} repetitions; restricted-mode oracle index "
                          f"(tracks the sample's probe positions), built in {obuild:.1f} s",
                "single_thread": {"value": units * reps1 / spent1, "unit": UNIT,
-                                 "repetitions": reps1}}
+                                 "repetitions": reps1},
+               "host": host_cpu()}
 
     clk = clocks.summary(t_wall0, t_wall1)
     line = {
