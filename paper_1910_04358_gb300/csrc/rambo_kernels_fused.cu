@@ -21,8 +21,8 @@ namespace {
 //   2. then take whole short queries from the short queue: the warp probes
 //      all k-mers, combines the lanes' slices into the bucket mask in shared
 //      memory and expands the answer itself, with no global round trip.
-// No warp ever waits on another.  Every k-mer of every query is probed; the
-// answers are the plain path's.
+// No warp ever waits on another.  With early exit off (the default) every
+// k-mer of every query is probed; the answers are the plain path's either way.
 constexpr int FUSED_THREADS = 256;
 
 struct FusedArgs {
@@ -186,10 +186,29 @@ __global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(Fused
             __syncwarp();
             skip = mask_dead(bm, f.p.Gw, f.e.B, f.e.R, lane);
             __syncwarp();
-            if (!skip && lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(k1 - k0));
         }
         if (!skip) {
-            const Slice<SW> s = fused_probe_range<SW, LPG, ETA>(f.p, start, k0, k1, lane, word0);
+            // early exit: probe the tile segment by segment; after each, the
+            // query's mask so far is this tile's part ANDed with what other
+            // tiles have flushed, and an empty repetition row ends the tile
+            Slice<SW> s;
+            slice_ones(s);
+            const uint64_t seg = f.early_exit ? f.segment : (k1 > k0 ? k1 - k0 : 1);
+            for (uint64_t a0 = k0; a0 < k1; a0 += seg) {
+                const uint64_t a1 = a0 + seg < k1 ? a0 + seg : k1;
+                slice_and(s, fused_probe_range<SW, LPG, ETA>(f.p, start, a0, a1, lane, word0));
+                if (!f.early_exit) continue;
+                if (lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(a1 - a0));
+                if (a1 >= k1) break;
+                if (sub == 0)
+#pragma unroll
+                    for (int w = 0; w < SW; ++w)
+                        bm[word0 + w] = s.w[w] & __ldcg(f.e.acc + q * f.p.Gw + word0 + w);
+                __syncwarp();
+                const bool dead = mask_dead(bm, f.p.Gw, f.e.B, f.e.R, lane);
+                __syncwarp();
+                if (dead) break;
+            }
             if (sub == 0) flush_slice<SW>(const_cast<uint32_t *>(f.e.acc), q, f.p.Gw, word0, s);
         }
         __threadfence();
