@@ -379,6 +379,7 @@ def run_stream(args):
     wl = synth.stream_workload()
     p = wl.params
     idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=local)
+    idx.set_tuning(query_path=args.query_path if args.query_path is not None else 1)
     info = idx.info
     to_dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
     n_epochs = min(wl.n_epochs, args.warmup + args.steps)
@@ -411,6 +412,30 @@ def run_stream(args):
     t_wall1 = time.time()
     clocks.stop()
     ms_step = q_ms / max(timed, 1)
+    # early exit on the last epoch's batch (the full index; identical answers,
+    # k-mers actually probed); reported beside the line, never as `value`
+    early = None
+    if not args.no_early_exit:
+        saved = idx.get_tuning()
+        ref = out.clone()
+        idx.set_tuning(early_exit=1, query_path=1, fused_short_max=max(saved["fused_short_max"], 1024))
+        idx.probed_kmers(reset=True)
+        idx.query_seqs_dev(d_qp, d_qo, out=out)
+        idx.sync()
+        probed = idx.probed_kmers(reset=True)
+        same = bool(torch.equal(out, ref))
+        ev[0].record(stream)
+        for _ in range(3):
+            idx.query_seqs_dev(d_qp, d_qo, out=out)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms_ee = ev[0].elapsed_time(ev[1]) / 3
+        nk_last = q.n_kmers(p.k)
+        early = {"ms_per_batch": ms_ee, "kmer_queries_per_s": nk_last / (ms_ee / 1e3),
+                 "seq_kmers_probed": probed, "seq_kmers": nk_last,
+                 "probed_frac": probed / max(nk_last, 1), "answers_identical": same,
+                 "batch": "the last epoch's query batch"}
+        idx.set_tuning(**saved)
     peak, peak_src = measured_peak_gbs()
     kpb = probe_bytes_per_kmer(info)
     line = {
@@ -428,6 +453,7 @@ def run_stream(args):
                      "frac": q_kmers * kpb / (q_ms / 1e3) / 1e9 / peak, "traffic": None,
                      "bytes_per_kmer": kpb, "peak_source": peak_src},
         "clocks": clocks.summary(t_wall0, t_wall1), "tuning": idx.get_tuning(),
+        "early_exit": early,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -506,6 +506,13 @@ class Index:
         return out
 
 
+def answer_docs(mask_row) -> np.ndarray:
+    """Document ids set in one answer mask (W uint32 words; document d is bit
+    d & 31 of word d >> 5)."""
+    words = np.ascontiguousarray(mask_row).view(np.uint32)
+    return np.nonzero(np.unpackbits(words.view(np.uint8), bitorder="little"))[0]
+
+
 def as_u32(t) -> np.ndarray:
     """A (n, W) int32 torch mask tensor as a host uint32 array."""
     return t.cpu().numpy().view(np.uint32)
