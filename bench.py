@@ -667,6 +667,10 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic,
                 "frac_of_spec_7900": achieved / 7900.0,
                 "dram_bytes_per_kmer": (traffic / n_seq_kmers) if traffic and n_seq_kmers else None,
+                # DRAM bytes the kernel really moves (ncu, per launch) over its live launch
+                # time: how busy the DRAM system is, 128-byte line fills included
+                "dram_gbs": (traffic / (dom_ms / 1e3) / 1e9) if traffic else None,
+                "dram_frac_of_peak": (traffic / (dom_ms / 1e3) / 1e9 / peak) if traffic else None,
                 "random_line_ceiling": "45-51 G random 128-byte lines/s measured "
                                        "(profiles/k_gather_random_records.md)",
                 "kernel": {0: "k_probe_seqs", 1: "k_fused_prep+k_fused",
