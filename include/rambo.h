@@ -360,6 +360,12 @@ typedef struct {
                                        /* many CTAs per SM (0 = as probe_ctas_per_sm;  */
                                        /* default 1), leaving room for the k-mer       */
                                        /* chunks whose copies out bound the call       */
+    uint32_t insert_mode;              /* Algorithm 1's bit setting: 0 = lanes hitting */
+                                       /* one word combine first (match + OR-reduce);  */
+                                       /* 1 = one 32-bit atomicOr per repetition; 2    */
+                                       /* (default) = as 1 with repetitions that share */
+                                       /* a 64-bit word merged into one 64-bit         */
+                                       /* atomicOr (32-bit when m * Gw is odd)         */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

@@ -531,6 +531,7 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     a.kcum = kcum;
     a.n = n;
     a.err = h->d_err;
+    a.mode = h->tune.insert_mode;
     {
         StageScope sc(h, RAMBO_STAGE_INSERT, s, 1);
         RAMBO_TRY(launch_insert(a, h->sm_count, s));
@@ -815,6 +816,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.host_direct = 0;
     h->tune.expand_tc = 0;
     h->tune.host_fused_ctas_per_sm = 1;
+    h->tune.insert_mode = 2;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -1255,7 +1257,8 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2 ||
         t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22) ||
         (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
-        t->host_direct > 1 || t->expand_tc > 1 || t->host_fused_ctas_per_sm > 32)
+        t->host_direct > 1 || t->expand_tc > 1 || t->host_fused_ctas_per_sm > 32 ||
+        t->insert_mode > 2)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

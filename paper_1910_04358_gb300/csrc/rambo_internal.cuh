@@ -218,6 +218,8 @@ struct InsertArgs {
     const uint64_t *kcum;      // n+1
     uint64_t n;
     uint32_t *err;
+    uint32_t mode;             // 0: warp-aggregated 32-bit atomics; 1: plain 32-bit;
+                               // 2: plain, repetitions sharing a 64-bit word merged
 };
 
 // Word documents (Section 5.4): term t is bytes [term_offs[t], term_offs[t+1])

@@ -189,7 +189,12 @@ __global__ void k_register(const uint32_t *doc_ids, uint64_t n, const uint32_t *
 // ------------------------------------------------------------------- insert
 constexpr int INSERT_THREADS = 256;
 
-template <int ETA>
+// MODE 0: lanes that hit the same index word combine their bits first
+// (match + OR-reduce) and one of them issues the atomic; MODE 1: every
+// (k-mer, probe, repetition) issues its own atomicOr; MODE 2: as 1, but the
+// bits of consecutive repetitions that fall into one 64-bit word go in one
+// 64-bit atomicOr (the repetitions' bits r*B + phi_r(d) ascend with r).
+template <int ETA, int MODE>
 __global__ void __launch_bounds__(INSERT_THREADS, 1) k_insert(InsertArgs a) {
     const int lane = threadIdx.x & 31;
     const uint64_t T = a.kcum[a.n];
@@ -234,17 +239,40 @@ __global__ void __launch_bounds__(INSERT_THREADS, 1) k_insert(InsertArgs a) {
                 if (jb + e >= a.eta) break;  // warp-uniform
                 const uint64_t h = mh_first_word(km, a.seed32 + jb + e);
                 const uint64_t p = a.m_pow2 ? (h & (a.m - 1)) : (h % a.m);
-                for (uint32_t r = 0; r < a.R; ++r) {
-                    uint64_t addr = ~0ULL;
-                    uint32_t bit = 0;
-                    if (val) {
-                        const uint32_t bb = r * a.B + a.phi[(uint64_t)d * a.R + r];
-                        addr = p * a.Gw + (bb >> 5);
-                        bit = 1u << (bb & 31);
+                if (MODE == 0) {
+                    for (uint32_t r = 0; r < a.R; ++r) {
+                        uint64_t addr = ~0ULL;
+                        uint32_t bit = 0;
+                        if (val) {
+                            const uint32_t bb = r * a.B + a.phi[(uint64_t)d * a.R + r];
+                            addr = p * a.Gw + (bb >> 5);
+                            bit = 1u << (bb & 31);
+                        }
+                        const uint32_t peers = __match_any_sync(FULL, addr);
+                        const uint32_t v = __reduce_or_sync(peers, bit);
+                        if (val && lane == __ffs(peers) - 1) atomicOr(a.index + addr, v);
                     }
-                    const uint32_t peers = __match_any_sync(FULL, addr);
-                    const uint32_t v = __reduce_or_sync(peers, bit);
-                    if (val && lane == __ffs(peers) - 1) atomicOr(a.index + addr, v);
+                } else if (val) {
+                    const uint64_t gbit = p * a.Gw * 32;  // first bit of the group
+                    if (MODE == 1) {
+                        for (uint32_t r = 0; r < a.R; ++r) {
+                            const uint64_t bb = gbit + r * a.B + a.phi[(uint64_t)d * a.R + r];
+                            atomicOr(a.index + (bb >> 5), 1u << (bb & 31));
+                        }
+                    } else {
+                        unsigned long long *idx64 = reinterpret_cast<unsigned long long *>(a.index);
+                        uint64_t cur = ~0ULL, bits = 0;
+                        for (uint32_t r = 0; r < a.R; ++r) {
+                            const uint64_t bb = gbit + r * a.B + a.phi[(uint64_t)d * a.R + r];
+                            if ((bb >> 6) != cur) {
+                                if (bits) atomicOr(idx64 + cur, (unsigned long long)bits);
+                                cur = bb >> 6;
+                                bits = 0;
+                            }
+                            bits |= 1ull << (bb & 63);
+                        }
+                        if (bits) atomicOr(idx64 + cur, (unsigned long long)bits);
+                    }
                 }
             }
         }
@@ -322,8 +350,18 @@ int blocks_per_sm(KernelT kernel, int threads) {
 
 template <int ETA>
 cudaError_t launch_insert_t(const InsertArgs &a, int sm_count, cudaStream_t s) {
-    static int occ = blocks_per_sm(k_insert<ETA>, INSERT_THREADS);
-    k_insert<ETA><<<sm_count * occ, INSERT_THREADS, 0, s>>>(a);
+    // 64-bit words need the index (m * Gw words) to end on a 64-bit boundary
+    const int mode = a.mode == 2 && (a.m * a.Gw) % 2 != 0 ? 1 : (int)a.mode;
+    if (mode == 1) {
+        static int occ = blocks_per_sm(k_insert<ETA, 1>, INSERT_THREADS);
+        k_insert<ETA, 1><<<sm_count * occ, INSERT_THREADS, 0, s>>>(a);
+    } else if (mode == 2) {
+        static int occ = blocks_per_sm(k_insert<ETA, 2>, INSERT_THREADS);
+        k_insert<ETA, 2><<<sm_count * occ, INSERT_THREADS, 0, s>>>(a);
+    } else {
+        static int occ = blocks_per_sm(k_insert<ETA, 0>, INSERT_THREADS);
+        k_insert<ETA, 0><<<sm_count * occ, INSERT_THREADS, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -172,7 +172,8 @@ TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_p
                  "expand_filter", "early_exit", "early_exit_segment",
                  "kmer_probe_ctas_per_sm", "host_chunk_kmers", "branch_priority",
                  "host_slots", "bin_region_kib", "bin_rows", "host_direct",
-                 "expand_tc", "host_fused_ctas_per_sm")
+                 "expand_tc", "host_fused_ctas_per_sm",
+                 "insert_mode")
 
 
 class _Tuning(C.Structure):

@@ -357,6 +357,30 @@ def test_sequence_batch_past_single_block_scan(rambo_lib):
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want), path
 
 
+@pytest.mark.parametrize("K,B,R,m", [
+    (120, 32, 4, 1 << 13),      # 16-byte groups: repetitions pair up in 64-bit words
+    (100, 16, 3, 5003),         # 8-byte groups, m odd: m * Gw odd -> 32-bit atomics
+    (64, 10, 3, 4097),          # 4-byte groups, m * Gw odd
+    (300, 100, 5, 1 << 12),     # 64-byte groups: repetitions in different words
+])
+def test_insert_modes_give_identical_index(rambo_lib, K, B, R, m):
+    p = synth.Params(K=K, B=B, R=R, m=m, eta=2, k=31, seed=K)
+    rng = np.random.default_rng(B * 13 + R)
+    corpus = synth.family_corpus(rng, p, n_seeds=max(1, K // 10), doc_len=500, sub_rate=0.02)
+    o = oracle_index(p, corpus)
+    base = None
+    for mode in (0, 1, 2):
+        idx = rambo_lib.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+        idx.set_tuning(insert_mode=mode)
+        idx.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
+        bits = idx.copy_index()
+        if base is None:
+            base = bits
+            assert_index_equal(idx, o, p)
+        assert np.array_equal(bits, base), mode
+        idx.close()
+
+
 # ------------------------------------------------ region-binned probing (path 2)
 
 @pytest.mark.parametrize("K,B,R,m,region_kib", [
