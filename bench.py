@@ -170,6 +170,8 @@ def host_cpu() -> str:
                     break
     except OSError:
         pass
+    arm_parts = {"0xd4f": "Arm Neoverse V2 (Grace)", "0xd40": "Arm Neoverse V1", "0xd4e": "Arm Cortex-X3"}
+    model = arm_parts.get(model.lower(), model)
     return f"{platform.machine()}, {os.cpu_count()} cores" + (f", {model}" if model else "")
 
 
