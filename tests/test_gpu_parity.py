@@ -282,6 +282,35 @@ def test_argument_errors(rambo_lib):
     with pytest.raises(rambo_lib.RamboError) as e:
         idx.sync()
     assert e.value.code == rambo_lib.RAMBO_EINVAL
+    # mixed batches: host offsets checked before anything runs, device
+    # workspace size and alignment checked before anything is enqueued
+    good_k = np.array([5, 7], np.uint64)
+    with pytest.raises(rambo_lib.RamboError) as e:
+        idx.query_batch(good_k, packed, np.array([5, 3], np.uint64))
+    assert e.value.code == rambo_lib.RAMBO_EINVAL
+    torch = _torch()
+    d_k, d_p = _dev(good_k, np.int64), _dev(packed, np.uint8)
+    d_o = _dev(np.array([0, 40], np.uint64), np.int64)
+    need = idx.workspace_bytes("kmers", 2) + idx.workspace_bytes("seqs", 1)
+    buf = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    with pytest.raises(rambo_lib.RamboError) as e:  # too small
+        idx.query_batch_dev(d_k, d_p, d_o, workspace=(ptr, need - 256))
+    assert e.value.code == rambo_lib.RAMBO_EINVAL
+    with pytest.raises(rambo_lib.RamboError) as e:  # not 256-byte aligned
+        idx.query_batch_dev(d_k, d_p, d_o, workspace=(ptr + 8, need))
+    assert e.value.code == rambo_lib.RAMBO_EINVAL
+    ok_k, ok_s = idx.query_batch_dev(d_k, d_p, d_o, workspace=(ptr, need))
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(ok_k), idx.query_kmers(good_k))
+    assert np.array_equal(rambo_lib.as_u32(ok_s), idx.query_seqs(packed, np.array([0, 40], np.uint64)))
+    # tuning knobs out of range are refused and leave the tuning unchanged
+    before = idx.get_tuning()
+    for bad in (dict(query_path=3), dict(host_slots=0), dict(host_slots=5), dict(bin_rows=3),
+                dict(insert_mode=3), dict(expand_tc=2), dict(early_exit_segment=100)):
+        with pytest.raises(rambo_lib.RamboError):
+            idx.set_tuning(**bad)
+    assert idx.get_tuning() == before
 
 
 # ------------------------------------------------------------------ folding
