@@ -334,7 +334,7 @@ typedef struct {
     uint32_t host_chunk_kmers;         /* host-buffer calls: k-mers per pipelined      */
                                        /* chunk (copy in, query, copy out); 0 = about  */
                                        /* 16 MiB of answers per chunk; the first chunk */
-                                       /* is a quarter of it                           */
+                                       /* is an eighth of it                           */
     uint32_t branch_priority;          /* mixed batches: 0 = both kinds at the caller's */
                                        /* stream priority; 1 = sequences, 2 = k-mers  */
                                        /* on a stream of the greatest priority        */

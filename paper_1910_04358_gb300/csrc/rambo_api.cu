@@ -21,6 +21,7 @@ struct rambo {
     cudaEvent_t ev_fork, ev_join, ev_join2;
     uint64_t *h_offs;        // page-locked staging of rebased host offsets
     size_t h_offs_bytes;
+    uint32_t *h_err;         // page-locked copy of the latched error word
     uint32_t *d_index;       // m * Gw words
     uint32_t *d_docbits;     // R * B * W words
     uint32_t *d_phi;         // K * R
@@ -549,6 +550,14 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
 
 // Reads and clears the latched error word on the handle's own stream (the
 // caller has already waited for the stream the kernels ran on).
+// Return code of a latched error word.
+int err_code(uint32_t e) {
+    if (e & (ERR_QUEUE | ERR_WAIT)) return RAMBO_ETIMEOUT;
+    if (e & ERR_DOC_RANGE) return RAMBO_ERANGE;
+    if (e & (ERR_KMER_CODE | ERR_OFFSETS)) return RAMBO_EINVAL;
+    return RAMBO_OK;
+}
+
 int read_and_clear_err(rambo_t *h) {
     uint32_t e = 0;
     RAMBO_TRY(cudaMemcpyAsync(&e, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream));
@@ -557,10 +566,7 @@ int read_and_clear_err(rambo_t *h) {
         RAMBO_TRY(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
         RAMBO_TRY(cudaStreamSynchronize(h->stream));
     }
-    if (e & (ERR_QUEUE | ERR_WAIT)) return RAMBO_ETIMEOUT;
-    if (e & ERR_DOC_RANGE) return RAMBO_ERANGE;
-    if (e & (ERR_KMER_CODE | ERR_OFFSETS)) return RAMBO_EINVAL;
-    return RAMBO_OK;
+    return err_code(e);
 }
 
 bool offsets_ok(uint64_t n, const uint64_t *offs) {
@@ -618,7 +624,7 @@ int reserve_host_offsets(rambo_t *h, size_t bytes) {
 
 // K-mers per chunk of a host-buffer k-mer batch: about 32 MiB of answers.
 // K-mers per chunk of a host-buffer k-mer batch: about 16 MiB of answers
-// unless the knob says otherwise.  The first chunk is a quarter of that, so
+// unless the knob says otherwise.  The first chunk is an eighth of that, so
 // the copy-out engine starts early.
 uint64_t host_chunk(const rambo_t *h, uint64_t n) {
     uint64_t c = h->tune.host_chunk_kmers;
@@ -630,7 +636,7 @@ uint64_t host_chunk(const rambo_t *h, uint64_t n) {
 }
 uint64_t host_chunk_begin(uint64_t c, uint64_t ck, uint64_t n) {
     if (c == 0) return 0;
-    const uint64_t first = ck >= 4 ? ck / 4 : ck;
+    const uint64_t first = ck >= 8 ? ck / 8 : ck;
     const uint64_t b = first + (c - 1) * ck;
     return b < n ? b : n;
 }
@@ -727,8 +733,26 @@ int query_batch_host(rambo_t *h, uint64_t nk, const uint64_t *kmers, uint32_t *o
             if (e != cudaSuccess) return bail(cuda_rc(e));
         }
     }
-    RAMBO_TRY(sync_own_streams(h));
-    return read_and_clear_err(h);
+    // join every stream of the call into the handle's stream and read the
+    // error word there: one wait for the whole call
+    for (int sl = 0; sl < slots; ++sl) {
+        if ((e = cudaEventRecord(h->ev_join, ks[sl])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess)
+            return bail(cuda_rc(e));
+    }
+    if (ns && ss != h->stream &&
+        ((e = cudaEventRecord(h->ev_join, ss)) != cudaSuccess ||
+         (e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess))
+        return bail(cuda_rc(e));
+    e = cudaMemcpyAsync(h->h_err, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(cuda_rc(e));
+    const uint32_t bits = *h->h_err;
+    if (bits) {
+        RAMBO_TRY(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+        RAMBO_TRY(cudaStreamSynchronize(h->stream));
+    }
+    return err_code(bits);
 }
 
 }  // namespace
@@ -778,6 +802,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
             if ((rc = cuda_rc(cudaStreamCreateWithPriority(&ps, cudaStreamNonBlocking, greatest))))
                 return fail(rc);
     }
+    if ((rc = cuda_rc(cudaMallocHost(reinterpret_cast<void **>(&h->h_err), sizeof(uint32_t))))) return fail(rc);
     if ((rc = cuda_rc(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)))) return fail(rc);
     if ((rc = cuda_rc(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)))) return fail(rc);
     if ((rc = cuda_rc(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming)))) return fail(rc);
@@ -844,6 +869,7 @@ int rambo_destroy(rambo_t *h) {
     }
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     if (h->h_offs) cudaFreeHost(h->h_offs);
+    if (h->h_err) cudaFreeHost(h->h_err);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_join2) cudaEventDestroy(h->ev_join2);
