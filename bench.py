@@ -226,20 +226,35 @@ def kernel_digest(kernel: str) -> str:
 # distributed plumbing (independent replicas; no data-path collective)
 
 
+_NCCL_DEVICE = None  # this rank's GPU when the process group is NCCL
+
+
 def dist_setup(backend: str):
+    global _NCCL_DEVICE
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group(backend=backend)
+        if backend == "nccl":
+            import torch
+            # bind the rank to its GPU before NCCL starts, so no collective
+            # has to guess the device
+            torch.cuda.set_device(local)
+            _NCCL_DEVICE = local
+            dist.init_process_group(backend=backend, device_id=torch.device(f"cuda:{local}"))
+        else:
+            dist.init_process_group(backend=backend)
     return rank, local, world
 
 
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
-        dist.barrier()
+        if _NCCL_DEVICE is not None:
+            dist.barrier(device_ids=[_NCCL_DEVICE])
+        else:
+            dist.barrier()
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
