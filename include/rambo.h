@@ -397,8 +397,9 @@ int rambo_probe_host_write(const void *src, void *dst_host, uint64_t bytes, uint
                            void *stream);
 
 /* Failure-detection check: enqueues on `stream` one kernel whose thread
- * waits on an mbarrier that nothing ever completes, with the same bounded
- * wait the tensor-core expansion uses, here of `spins` polls (1..2^22).  The
+ * waits on an mbarrier that nothing ever completes, with the bounded polling
+ * wait that the tensor-core expansion's warps use to hand work to each other,
+ * here of `spins` polls (1..2^22) instead of the kernel's 2^26.  The
  * wait runs out and latches the error that the next rambo_sync on that
  * stream reports as RAMBO_ETIMEOUT; nothing faults or hangs, and the handle
  * stays usable.  RAMBO_EINVAL for spins out of range. */

@@ -54,7 +54,8 @@ constexpr uint32_t TC_LBO = 128;            // bytes between 16-byte column chun
 constexpr uint32_t TC_TMEM_COLS = TC_NBUF * TC_N;  // all 512 columns
 constexpr size_t TC_SMEM_MIN = 120 * 1024;  // keeps one CTA (one TMEM owner) per SM
 constexpr size_t TC_SMEM_MAX = 216 * 1024;  // leaves room for a fused-query CTA
-constexpr uint64_t TC_WAIT_SPINS = 1ull << 22;  // try_wait rounds before giving up
+constexpr uint64_t TC_WAIT_SPINS = 1ull << 22;  // suspending try_wait rounds before giving up
+constexpr uint64_t TC_POLL_SPINS = 1ull << 26;  // non-suspending polls before giving up (about a second)
 
 constexpr uint32_t TC_EPI_PARTS = TC_EPI_WARPS / 4;         // column parts of a chunk (per lane quadrant)
 constexpr uint32_t TC_EPI_COLS = TC_N / TC_EPI_PARTS;         // columns per epilogue warp and chunk
@@ -130,18 +131,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
     return false;
 }
 
-// A wait that nothing completes: one thread waits on a fresh mbarrier (no
-// arrivals are ever made) with the kernels' bounded wait and latches ERR_WAIT
-// when it gives up.  It exercises the timeout path of the tensor-core
-// expansion without any fault or hang.
-__global__ void k_wait_expiry(uint32_t *err, uint64_t spins) {
-    __shared__ unsigned long long bar;
-    if (threadIdx.x != 0) return;
-    const uint32_t b = smem_u32(&bar);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    if (!mbar_wait(b, 0, spins)) atomicOr(err, ERR_WAIT);
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -187,19 +176,33 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait of one role, polling without suspending the warp (each
 // hand-off is on the critical path of a two-deep pipeline): false when the
-// abort flag is raised (polled every 64 rounds) or when this wait runs out,
-// which raises the flag and latches ERR_WAIT.
+// abort flag is raised (polled every 64 rounds) or when this wait runs out
+// after `spins` polls, which raises the flag and latches ERR_WAIT.
 __device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort,
-                                          uint32_t *err) {
+                                          uint32_t *err, uint64_t spins = TC_POLL_SPINS) {
     for (uint64_t i = 0;; ++i) {
         if (mbar_test_wait(bar, parity)) return true;
         if ((i & 63) == 63 && *abort) return false;
-        if (i >= TC_WAIT_SPINS) {
+        if (i >= spins) {
             *abort = 1;
             atomicOr(err, ERR_WAIT);
             return false;
         }
     }
+}
+
+// A wait that nothing completes: one thread waits on a fresh mbarrier (no
+// arrivals are ever made) with the roles' bounded polling wait, which runs
+// out after `spins` polls and latches ERR_WAIT.  It exercises the timeout
+// path of the tensor-core expansion without any fault or hang.
+__global__ void k_wait_expiry(uint32_t *err, uint64_t spins) {
+    __shared__ unsigned long long bar;
+    __shared__ uint32_t abort;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    abort = 0;
+    mbar_init(b, 1);
+    role_wait(b, 0, &abort, err, spins);
 }
 
 // Chunk of A at column `bit` (a multiple of 16) from the 16 mask bits v found
