@@ -32,6 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_1910_04358_gb300.autotune import effective_path  # noqa: E402  (no torch, no library)
+
 METRIC = "k-mer queries/s and query bp/s on 1 GB300 (bit-exact vs oracle); serving p50/p99 ms"
 UNIT = "k-mer queries/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -173,17 +175,6 @@ def host_cpu() -> str:
     arm_parts = {"0xd4f": "Arm Neoverse V2 (Grace)", "0xd40": "Arm Neoverse V1", "0xd4e": "Arm Cortex-X3"}
     model = arm_parts.get(model.lower(), model)
     return f"{platform.machine()}, {os.cpu_count()} cores" + (f", {model}" if model else "")
-
-
-def effective_path(tuning, info) -> int:
-    """Sequence query path the library takes for this tuning and geometry (the
-    binding always passes a workspace large enough for path 2)."""
-    g = info["group_bytes"]
-    if tuning["query_path"] == 2 and g <= 16:
-        return 2
-    if tuning["query_path"] >= 1 and g <= 512:
-        return 1
-    return 0
 
 
 def probe_algorithmic_bytes(info, n_kmers: int, n_queries: int, n_bases: int) -> int:
@@ -398,6 +389,18 @@ def run_stream(args):
     idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=local)
     idx.set_tuning(query_path=args.query_path if args.query_path is not None else 1)
     info = idx.info
+    # the epochs' batches differ a little in k-mers per query, so the cached
+    # tuning is kept per index geometry and epoch batch size; without one, the
+    # autotuner runs on the first epoch's batch, after that epoch
+    tuned, cached, tuning_source = None, None, "default (query_path=1)"
+    autotuning = not args.no_autotune and args.query_path is None
+    if autotuning:
+        from paper_1910_04358_gb300 import autotune
+        key = autotune.cache_key(idx, wl.queries_per_epoch, 0).rsplit("_kpq", 1)[0] + "_stream"
+        cached = None if args.retune else autotune.load_cached(autotune.CACHE_FILE, key)
+        if cached:
+            idx.set_tuning(**cached)
+            tuning_source = f"cached ({os.path.relpath(autotune.CACHE_FILE, ROOT)})"
     to_dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
     n_epochs = min(wl.n_epochs, args.warmup + args.steps)
     stream = torch.cuda.current_stream()
@@ -425,6 +428,12 @@ def run_stream(args):
             q_kmers += q.n_kmers(p.k)
             q_bp += q.n_bases
             timed += 1
+        if e == 0 and autotuning and not cached:
+            tuned = autotune.autotune(idx, lambda: idx.query_seqs_dev(d_qp, d_qo, out=out),
+                                      lambda: [out], reps=5)
+            log(f"[autotune] best {tuned['best']} {tuned['ms']:.4f} ms/batch")
+            autotune.store_cached(autotune.CACHE_FILE, key, tuned["best"])
+            tuning_source = "autotuned in this run (first epoch's batch)"
     idx.sync()
     t_wall1 = time.time()
     clocks.stop()
@@ -470,6 +479,8 @@ def run_stream(args):
                      "frac": q_kmers * kpb / (q_ms / 1e3) / 1e9 / peak, "traffic": None,
                      "bytes_per_kmer": kpb, "peak_source": peak_src},
         "clocks": clocks.summary(t_wall0, t_wall1), "tuning": idx.get_tuning(),
+        "tuning_source": tuning_source,
+        "autotune": ({"trials": len(tuned["trials"]), "best_ms": tuned["ms"]} if tuned else None),
         "early_exit": early,
     }
     if rank == 0:

@@ -7,8 +7,13 @@ warp takes, the fused path's tile size and short-query threshold, and the
 expansion grid and byte-table policy.  It times the batch under each
 candidate with CUDA events on the launching stream and insists that every
 candidate returns exactly the same answer bits as the first one (the knobs
-change launch shapes only).  Search is coordinate descent: one knob at a
-time, in the order of KNOBS, keeping the best value before moving on.
+change launch shapes only).  Search: for every query path that this index
+geometry actually runs (a requested path the library cannot take for these
+groups falls back to another, and is then not a separate candidate), a
+coordinate descent over the other knobs, one knob at a time in the order of
+KNOBS, keeping the best value before moving on; the best of the paths wins.
+Knobs of a path that does not run (the fused path's tile and short-query
+threshold, the binned path's regions) are not varied.
 """
 from __future__ import annotations
 
@@ -55,46 +60,83 @@ def _time(run, reps: int):
     return best
 
 
-def autotune(idx, run, outputs, reps: int = 7, knobs=KNOBS, verbose: bool = False) -> dict:
-    """Tunes `idx` for the batch that `run()` enqueues on the current stream.
+def effective_path(tuning, info) -> int:
+    """Sequence query path the library takes for this tuning and geometry (the
+    binding always passes a workspace large enough for path 2): the binned
+    path for groups of at most 16 bytes, the fused path for groups of at most
+    512 bytes, else the separate launches."""
+    g = info["group_bytes"]
+    if tuning["query_path"] == 2 and g <= 16:
+        return 2
+    if tuning["query_path"] >= 1 and g <= 512:
+        return 1
+    return 0
 
-    `outputs()` returns the tensors holding the batch's answers after a run;
-    every candidate's answers must equal the first candidate's bit for bit.
-    Leaves the best tuning set on `idx` and returns
-    {"best": tuning, "ms": best time, "trials": [...]}.
-    """
+
+def _descend(idx, run, outputs, ref, start, knobs, reps, info, trials, verbose):
+    """Coordinate descent from `start` over `knobs`; returns (best, ms)."""
     import torch
-    base = idx.get_tuning()
-    run()
-    idx.sync()
-    ref = [t.clone() for t in outputs()]
-    best_cfg, best_ms = dict(base), _time(run, reps)
-    trials = [{"tuning": dict(base), "ms": best_ms}]
+    idx.set_tuning(**start)
+    best_cfg, best_ms = dict(start), _time(run, reps)
+    trials.append({"tuning": dict(start), "ms": best_ms})
+    path = effective_path(start, info)
     for knob, values in knobs:
+        if knob in ("fused_tile_kmers", "fused_short_max") and path != 1:
+            continue
+        if knob in ("bin_region_kib", "bin_rows") and path != 2:
+            continue
         for v in values:
             if best_cfg.get(knob) == v:
                 continue
             cand = dict(best_cfg)
             cand[knob] = v
-            if knob in ("fused_tile_kmers", "fused_short_max") and cand["query_path"] != 1:
-                continue
-            if knob in ("bin_region_kib", "bin_rows") and cand["query_path"] != 2:
-                continue
             idx.set_tuning(**cand)
             ms = _time(run, reps)
             idx.sync()
-            got = outputs()
-            for a, b in zip(ref, got):
+            for a, b in zip(ref, outputs()):
                 if not torch.equal(a, b):
-                    idx.set_tuning(**base)
                     raise RuntimeError(f"tuning {cand} changed the answers")
             trials.append({"tuning": cand, "ms": ms})
             if verbose:
-                print(f"autotune {knob}={v}: {ms:.4f} ms (best {best_ms:.4f})", flush=True)
+                print(f"autotune path {path} {knob}={v}: {ms:.4f} ms (best {best_ms:.4f})", flush=True)
             if ms < best_ms:
                 best_cfg, best_ms = cand, ms
-    idx.set_tuning(**best_cfg)
-    return {"best": best_cfg, "ms": best_ms, "trials": trials}
+    return best_cfg, best_ms
+
+
+def autotune(idx, run, outputs, reps: int = 7, knobs=KNOBS, verbose: bool = False) -> dict:
+    """Tunes `idx` for the batch that `run()` enqueues on the current stream.
+
+    `outputs()` returns the tensors holding the batch's answers after a run;
+    every candidate's answers must equal the first run's bit for bit.
+    Leaves the best tuning set on `idx` and returns
+    {"best": tuning, "ms": best time, "trials": [...]}.
+    """
+    base = idx.get_tuning()
+    info = idx.info
+    run()
+    idx.sync()
+    ref = [t.clone() for t in outputs()]
+    paths = dict(knobs).get("query_path", (base["query_path"],))
+    rest = [(k, v) for k, v in knobs if k != "query_path"]
+    starts, seen = [], set()
+    for qp in paths:
+        start = dict(base, query_path=qp)
+        ep = effective_path(start, info)
+        if ep not in seen:
+            seen.add(ep)
+            starts.append(start)
+    trials, best = [], None
+    try:
+        for start in starts:
+            cfg, ms = _descend(idx, run, outputs, ref, start, rest, reps, info, trials, verbose)
+            if best is None or ms < best[1]:
+                best = (cfg, ms)
+    except Exception:
+        idx.set_tuning(**base)
+        raise
+    idx.set_tuning(**best[0])
+    return {"best": best[0], "ms": best[1], "trials": trials}
 
 
 def cache_key(idx, n_queries: int, n_kmers: int) -> str:

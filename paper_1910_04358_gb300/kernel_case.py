@@ -1,12 +1,15 @@
 """Small, self-contained launches of one query stage, for profiling.
 
-  python -m paper_1910_04358_gb300.kernel_case --case kmers|seqs [--workload medium|large]
-         [--reps N] [--query-path 0|1]
+  python -m paper_1910_04358_gb300.kernel_case --case kmers|seqs
+         [--workload medium|large|stream] [--reps N] [--query-path 0|1]
 
 Builds the workload's index on cuda:0, then runs the chosen query batch
 `reps` times (kmers: the medium workload's 10^6 single 31-mers; seqs: its
 sequence batch) so a profiler can capture single launches of the probe,
-expansion or fused kernels on a realistic index.
+expansion or fused kernels on a realistic index.  The stream workload
+inserts its first `--epochs` epochs of documents (its full document
+geometry: 10^5 document bits per answer, R = 6, B = 316) and queries the
+last epoch's batch.
 """
 from __future__ import annotations
 
@@ -19,7 +22,7 @@ import numpy as np
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", choices=["kmers", "seqs"], default="kmers")
-    ap.add_argument("--workload", choices=["medium", "large"], default="medium")
+    ap.add_argument("--workload", choices=["medium", "large", "stream"], default="medium")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--query-path", type=int, default=0)
     ap.add_argument("--tune", nargs="*", default=[], help="tuning knobs as name=value")
@@ -28,10 +31,13 @@ def main(argv=None):
     ap.add_argument("--n-docs", type=int, default=None, help="fewer documents (same geometry)")
     ap.add_argument("--m", type=int, default=None, help="bits per filter (smaller index)")
     ap.add_argument("--n-queries", type=int, default=None, help="fewer sequence queries (large)")
+    ap.add_argument("--epochs", type=int, default=3, help="insert epochs before the query (stream)")
     a = ap.parse_args(argv)
     import torch
 
     from . import rambo, synth
+    if a.workload == "stream":
+        return stream_case(a)
     if a.workload == "medium":
         corpus, kmers, q = synth.medium_workload(n_docs=a.n_docs)
     else:
@@ -69,6 +75,39 @@ def main(argv=None):
         out = torch.empty((q.n, idx.W), dtype=torch.int32, device="cuda")
         for _ in range(a.reps):
             idx.query_seqs_dev(dp, do, out=out)
+    idx.sync()
+    print("ok", a.case, a.workload, int(out.sum().item()))
+    return 0
+
+
+def stream_case(a):
+    import torch
+
+    from . import rambo, synth
+    if a.case != "seqs":
+        raise SystemExit("the stream workload has sequence queries only")
+    wl = synth.stream_workload(m=a.m)
+    p = wl.params
+    dev = lambda x, dt: torch.from_numpy(np.ascontiguousarray(x).view(dt)).cuda()
+    idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=0)
+    idx.set_tuning(query_path=a.query_path if a.query_path else 1)
+    if a.tuning_from_cache:  # the tuning bench.py keeps for this geometry's epoch batches
+        from . import autotune
+        key = autotune.cache_key(idx, wl.queries_per_epoch, 0).rsplit("_kpq", 1)[0] + "_stream"
+        cached = autotune.load_cached(autotune.CACHE_FILE, key)
+        if cached:
+            idx.set_tuning(**cached)
+    if a.tune:
+        idx.set_tuning(**{kv.split("=")[0]: int(kv.split("=")[1]) for kv in a.tune})
+    for e in range(max(1, min(a.epochs, wl.n_epochs))):
+        (ids, packed, offs), q = wl.epoch(e)
+        idx.insert_batch_dev(dev(ids.astype(np.int32), np.int32), dev(packed, np.uint8),
+                             dev(offs, np.int64))
+    idx.sync()
+    dp, do = dev(q.packed, np.uint8), dev(q.offsets, np.int64)
+    out = torch.empty((q.n, idx.W), dtype=torch.int32, device="cuda")
+    for _ in range(a.reps):
+        idx.query_seqs_dev(dp, do, out=out)
     idx.sync()
     print("ok", a.case, a.workload, int(out.sum().item()))
     return 0

@@ -24,3 +24,72 @@ def test_bench_effective_path():
     assert bench.effective_path(t(1), {"group_bytes": 512}) == 1
     assert bench.effective_path(t(1), {"group_bytes": 1024}) == 0
     assert bench.effective_path(t(0), {"group_bytes": 16}) == 0
+
+
+class _FakeIndex:
+    """Tuning state and geometry of an index, without a device."""
+
+    def __init__(self, group_bytes):
+        from paper_1910_04358_gb300 import autotune
+        self.info = {"group_bytes": group_bytes}
+        self.t = {k: vals[0] for k, vals in autotune.KNOBS}
+        self.t.update(query_path=0, fused_tile_kmers=1024, fused_short_max=1024)
+
+    def get_tuning(self):
+        return dict(self.t)
+
+    def set_tuning(self, **kw):
+        self.t.update(kw)
+
+    def sync(self):
+        pass
+
+
+def _fused_cost(t, info):
+    # separate launches beat the fused path at its default tile and threshold,
+    # but the fused path with small tiles and a low threshold beats both
+    from paper_1910_04358_gb300.autotune import effective_path
+    p = effective_path(t, info)
+    if p == 0:
+        return 1.10
+    if p == 2:
+        return 1.20 - (0.01 if t["bin_rows"] == 4 else 0.0)
+    return 1.105 - 0.03 * (t["fused_tile_kmers"] == 256) - 0.03 * (t["fused_short_max"] == 256)
+
+
+def test_autotune_descends_from_every_path_the_geometry_runs(monkeypatch):
+    import torch
+    from paper_1910_04358_gb300 import autotune
+    out = torch.zeros(4, dtype=torch.int32)
+    # 256-byte groups: a request for the binned path runs the fused one, so
+    # only paths 0 and 1 are searched, and the fused knobs are tuned
+    idx = _FakeIndex(256)
+    monkeypatch.setattr(autotune, "_time", lambda run, reps: _fused_cost(idx.t, idx.info))
+    res = autotune.autotune(idx, lambda: None, lambda: [out], reps=1)
+    assert autotune.effective_path(res["best"], idx.info) == 1
+    assert res["best"]["fused_tile_kmers"] == 256 and res["best"]["fused_short_max"] == 256
+    assert not any(tr["tuning"]["query_path"] == 2 for tr in res["trials"])
+    assert not any(tr["tuning"]["bin_rows"] != dict(autotune.KNOBS)["bin_rows"][0] for tr in res["trials"])
+    assert idx.get_tuning() == res["best"]
+    # 16-byte groups: three distinct paths; the binned knobs vary only there
+    idx = _FakeIndex(16)
+    monkeypatch.setattr(autotune, "_time", lambda run, reps: _fused_cost(idx.t, idx.info))
+    res = autotune.autotune(idx, lambda: None, lambda: [out], reps=1)
+    assert {tr["tuning"]["query_path"] for tr in res["trials"]} == {0, 1, 2}
+    assert all(tr["tuning"]["query_path"] == 2 for tr in res["trials"]
+               if tr["tuning"]["bin_rows"] == 4)
+    assert res["best"]["query_path"] == 1
+
+
+def test_autotune_rejects_a_candidate_that_changes_the_answers(monkeypatch):
+    import pytest
+    import torch
+    from paper_1910_04358_gb300 import autotune
+    idx = _FakeIndex(16)
+    start = idx.get_tuning()
+    good, bad = torch.zeros(4, dtype=torch.int32), torch.ones(4, dtype=torch.int32)
+    monkeypatch.setattr(autotune, "_time", lambda run, reps: 1.0)
+    outputs = lambda: [bad if idx.t["fused_short_max"] == 64 else good]
+    with pytest.raises(RuntimeError):
+        autotune.autotune(idx, lambda: None, outputs, reps=1)
+    assert idx.get_tuning() == start
