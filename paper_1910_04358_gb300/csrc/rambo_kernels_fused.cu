@@ -152,9 +152,11 @@ template <int SW, int LPG, int ETA, int C>
 // lanes; one-lane groups keep 16 loads per lane in flight at two
 __global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(FusedArgs f) {
     __shared__ uint32_t bm_smem[FUSED_THREADS / 32][128];
+    __shared__ uint32_t list_smem[FUSED_THREADS / 32][EXPAND_LIST_MAX];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     uint32_t *bm = bm_smem[wib];
+    uint32_t *list = list_smem[wib];
     const int sub = lane / LPG;
     const uint32_t word0 = (lane % LPG) * SW;
     const uint32_t n_short = f.counters[0];
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(Fused
             __threadfence();
             for (uint32_t w = lane; w < f.p.Gw; w += 32) bm[w] = __ldcg(f.e.acc + q * f.p.Gw + w);
             __syncwarp();
-            for (uint32_t c = 0; c < chunks; ++c) expand_one<C>(f.e, bm, q, c * 32 * C + lane, lane);
+            expand_query<C>(f.e, bm, q, chunks, lane, list);
             __syncwarp();
         }
     }
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(Fused
 #pragma unroll
             for (int w = 0; w < SW; ++w) bm[word0 + w] = sl.w[w];
         __syncwarp();
-        for (uint32_t c = 0; c < chunks; ++c) expand_one<C>(f.e, bm, q, c * 32 * C + lane, lane);
+        expand_query<C>(f.e, bm, q, chunks, lane, list);
         __syncwarp();
     }
 }

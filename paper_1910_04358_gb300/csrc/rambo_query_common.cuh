@@ -260,6 +260,122 @@ __device__ __forceinline__ void expand_one(const ExpandArgs &a, const uint32_t *
     else expand_unit_sparse<C>(a, bm, q, w0);
 }
 
+// Passing buckets of one query, decoded once for all of its answer chunks
+// (Algorithm 2's union needs only the buckets whose bit survived): the warp
+// writes the indices i = r*B + b of the set bits of bm (bits past R*B
+// ignored) in increasing order into `list` (EXPAND_LIST_MAX words of the
+// warp's shared memory) and returns how many there are, or
+// EXPAND_LIST_MAX + 1 when more pass (the caller then scans the mask per
+// chunk).  *dead is set when some repetition has no passing bucket: the
+// answer is then empty.
+constexpr uint32_t EXPAND_LIST_MAX = 32;
+
+__device__ __forceinline__ uint32_t bucket_list(const uint32_t *bm, uint32_t R, uint32_t B, uint32_t *list,
+                                                int lane, bool *dead) {
+    const uint32_t RB = R * B;
+    const uint32_t nw = (RB + 31) / 32;
+    uint32_t total = 0;
+    for (uint32_t base = 0; base < nw; base += 32) {
+        const uint32_t w = base + lane;
+        uint32_t v = w < nw ? bm[w] : 0u;
+        if (w == nw - 1 && (RB & 31)) v &= (1u << (RB & 31)) - 1u;
+        const uint32_t cnt = __popc(v);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += o;
+        }
+        const uint32_t block = __shfl_sync(FULL, incl, 31);
+        if (total + block > EXPAND_LIST_MAX) {
+            __syncwarp();
+            return EXPAND_LIST_MAX + 1;
+        }
+        uint32_t at = total + incl - cnt;
+        while (v) {
+            list[at++] = 32 * w + __ffs(v) - 1;
+            v &= v - 1;
+        }
+        total += block;
+    }
+    __syncwarp();
+    // every repetition present?  the entries are sorted, so count the
+    // repetition changes along the list
+    bool first = false;
+    if ((uint32_t)lane < total) {
+        const uint32_t r = list[lane] / B;
+        first = lane == 0 || list[lane - 1] / B != r;
+    }
+    *dead = (uint32_t)__popc(__ballot_sync(FULL, first)) < R;
+    return total;
+}
+
+// One chunk of a query's answer (lane words w0 + 32c, c < C) from its
+// decoded bucket list: rows of the same repetition ORed, repetitions ANDed.
+// Every repetition has an entry unless `dead`, so a repetition boundary is
+// crossed exactly when an entry reaches the next repetition's first bucket.
+template <int C>
+__device__ __forceinline__ void expand_unit_list(const ExpandArgs &a, const uint32_t *list, uint32_t n,
+                                                 bool dead, uint64_t q, uint32_t w0) {
+    uint32_t res[C], o[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        res[c] = dead ? 0u : FULL;
+        o[c] = 0;
+    }
+    if (!dead) {
+        uint32_t next = (list[0] / a.B + 1) * a.B;  // first bucket index of the next repetition
+        for (uint32_t t = 0; t < n; ++t) {
+            const uint32_t i = list[t];
+            if (i >= next) {
+                uint32_t nz = 0;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    res[c] &= o[c];
+                    o[c] = 0;
+                    nz |= res[c];
+                }
+                next += a.B;
+                if (!__any_sync(FULL, nz)) break;  // the intersection is already empty
+            }
+            const uint32_t *row = a.docbits + (uint64_t)i * a.W;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const uint32_t w = w0 + 32 * c;
+                if (w < a.W) o[c] |= __ldg(row + w);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) res[c] &= o[c];
+    }
+    uint32_t *out = a.out + q * a.W;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const uint32_t w = w0 + 32 * c;
+        if (w < a.W) out[w] = res[c];
+    }
+}
+
+// The whole answer of one query (chunks of 32*C words), by one warp: with
+// several chunks and no byte table, the passing buckets are decoded once
+// into `list` (EXPAND_LIST_MAX words of the warp's shared memory) and each
+// chunk walks them; otherwise, or when more buckets pass, each chunk scans
+// the mask itself.
+template <int C>
+__device__ __forceinline__ void expand_query(const ExpandArgs &a, const uint32_t *bm, uint64_t q,
+                                             uint32_t chunks, int lane, uint32_t *list) {
+    if (chunks > 1 && !a.tab) {
+        bool dead = false;
+        const uint32_t n = bucket_list(bm, a.R, a.B, list, lane, &dead);
+        if (n <= EXPAND_LIST_MAX) {
+            for (uint32_t c = 0; c < chunks; ++c) expand_unit_list<C>(a, list, n, dead, q, c * 32 * C + lane);
+            __syncwarp();  // the list is the next query's
+            return;
+        }
+    }
+    for (uint32_t c = 0; c < chunks; ++c) expand_one<C>(a, bm, q, c * 32 * C + lane, lane);
+}
+
 template <typename KernelT>
 int blocks_per_sm(KernelT kernel, int threads, size_t smem) {
     int n = 0;

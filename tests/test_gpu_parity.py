@@ -167,6 +167,29 @@ def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k, path):
     assert np.array_equal(idx.query_kmers(kmers), o.query_kmers(kmers))
 
 
+@pytest.mark.parametrize("path", [0, 1])
+def test_many_documents_several_answer_chunks(rambo_lib, path):
+    # more than 4096 documents, so an answer spans several chunks: the fused
+    # path decodes each query's passing buckets once for all of them, or scans
+    # the mask per chunk when more than 32 buckets pass.  Long queries from
+    # documents keep a few buckets, single k-mers dozens, and sequences
+    # shorter than k all of them (every inserted document answers).
+    p = synth.Params(K=5000, B=316, R=6, m=1 << 15, eta=2, k=31, seed=77)
+    rng = np.random.default_rng(77)
+    corpus = synth.family_corpus(rng, p, n_seeds=50, doc_len=500, sub_rate=0.01)
+    lengths = np.concatenate([rng.integers(31, 400, size=200), np.full(40, 31), np.full(5, 10)])
+    q = synth.sample_queries(rng, corpus, lengths, 0.6)
+    o = oracle_index(p, corpus)
+    idx = gpu_index(rambo_lib, p, corpus)
+    idx.set_tuning(query_path=path, fused_tile_kmers=64, fused_short_max=40)
+    got = gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets)
+    want = o.query_seqs(q.packed, q.offsets)
+    assert np.array_equal(got, want)
+    # the mix reaches both expansion routes of the fused path
+    pops = np.array([len(oracle.mask_to_docs(w)) for w in want])
+    assert (pops[-5:] == p.K).all() and (pops[:200] < p.K).all()
+
+
 def test_tuning_knobs_do_not_change_results(rambo_lib):
     p = synth.Params(K=300, B=40, R=4, m=1 << 13, eta=2, k=31, seed=4)
     rng = np.random.default_rng(77)
