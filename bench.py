@@ -190,6 +190,20 @@ def source_digest(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def measured_traffic_per_kmer(workload: str, kernel: str):
+    """dram bytes per probed k-mer from a committed ncu capture of one batch
+    (for workloads whose batches differ in size), if the sources are
+    unchanged since the counters were taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            e = json.load(f)[workload][kernel]
+        if e.get("source_sha") != kernel_digest(kernel) or not e.get("kmers_per_launch"):
+            return None
+        return float(e["dram_bytes_per_launch"]) / float(e["kmers_per_launch"])
+    except Exception:
+        return None
+
+
 def measured_traffic(workload: str, kernel: str):
     """dram bytes per launch from a committed ncu capture, if the kernel's
     source (and the shared device header) has not changed since the counters
@@ -464,6 +478,10 @@ def run_stream(args):
         idx.set_tuning(**saved)
     peak, peak_src = measured_peak_gbs()
     kpb = probe_bytes_per_kmer(info)
+    # DRAM bytes of the fused launch, scaled from the captured batch by k-mers
+    per_kmer = measured_traffic_per_kmer("stream", "k_fused") \
+        if effective_path(idx.get_tuning(), info) == 1 else None
+    traffic = per_kmer * q_kmers / max(timed, 1) if per_kmer else None
     line = {
         "metric": METRIC, "value": q_kmers / (q_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": timed, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -476,7 +494,12 @@ def run_stream(args):
         "insert": {"kmers_per_s": ins_kmers / (ins_ms / 1e3), "ms_per_epoch": ins_ms / max(timed, 1)},
         "roofline": {"bound": "hbm", "kernel": "query step (all query kernels)",
                      "achieved": q_kmers * kpb / (q_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": q_kmers * kpb / (q_ms / 1e3) / 1e9 / peak, "traffic": None,
+                     "frac": q_kmers * kpb / (q_ms / 1e3) / 1e9 / peak, "traffic": traffic,
+                     "dram_bytes_per_kmer": per_kmer,
+                     "dram_gbs": traffic / (ms_step / 1e3) / 1e9 if traffic else None,
+                     "dram_frac_of_peak": traffic / (ms_step / 1e3) / 1e9 / peak if traffic else None,
+                     "traffic_source": ("profiles/traffic.json (one batch's ncu capture, scaled by "
+                                        "k-mers per batch)") if traffic else None,
                      "bytes_per_kmer": kpb, "peak_source": peak_src},
         "clocks": clocks.summary(t_wall0, t_wall1), "tuning": idx.get_tuning(),
         "tuning_source": tuning_source,
