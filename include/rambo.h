@@ -365,7 +365,17 @@ typedef struct {
                                        /* 1 = one 32-bit atomicOr per repetition; 2    */
                                        /* (default) = as 1 with repetitions that share */
                                        /* a 64-bit word merged into one 64-bit         */
-                                       /* atomicOr (32-bit when m * Gw is odd)         */
+                                       /* atomicOr (32-bit when m * Gw is odd); 3 =    */
+                                       /* binned by index region (bin_region_kib):     */
+                                       /* probes are first written as 8-byte records   */
+                                       /* per region, then applied region by region so */
+                                       /* the atomics hit L2 -- for indexes of at most */
+                                       /* 128 regions, K <= 2^24 and m <= 2^40, else   */
+                                       /* as 2.  Choosing 3 reserves the record buffer */
+                                       /* (RAMBO_ENOMEM if it cannot be had)           */
+    uint32_t insert_bin_records;       /* insert_mode 3: records the buffer holds      */
+                                       /* (8 bytes each; 0 = 2^28, else >= 4096); a    */
+                                       /* batch is applied in chunks that fill it      */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

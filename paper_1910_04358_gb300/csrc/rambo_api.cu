@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "rambo.h"
+#include "rambo_insert_binned.cuh"
 #include "rambo_internal.cuh"
 
 using namespace rgpu;
@@ -32,6 +33,9 @@ struct rambo {
     bool any_inserted;       // set by the first insert call
     uint32_t *d_tab;         // byte table for the expansion (or null)
     uint32_t *d_ntab;        // nibble table for the expansion (or null)
+    unsigned long long *d_bins;  // binned insert: records (insert_mode 3), or null
+    uint32_t *d_bin_count;       // binned insert: per-bin counts and the unit counter
+    uint64_t bins_records;       // records d_bins holds
     rambo_tuning_t tune;
     // profiling
     uint32_t prof_mask;
@@ -533,7 +537,27 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     a.n = n;
     a.err = h->d_err;
     a.mode = h->tune.insert_mode;
-    {
+    uint32_t rshift = 0;
+    const uint32_t nbins =
+        a.mode == 3 && h->d_bins
+            ? binned_insert_bins(g.m, g.Gw * 4, g.K,
+                                 (uint64_t)(h->tune.bin_region_kib ? h->tune.bin_region_kib : 32768) * 1024,
+                                 &rshift)
+            : 0;
+    if (nbins) {
+        // chunks of the flat k-mer index sized to fill the record buffer
+        // (k-mers <= bases; chunks past the batch's k-mers do nothing)
+        BinnedInsert b{h->d_bins, h->d_bin_count, h->bins_records / nbins, nbins, rshift};
+        const uint64_t per = h->bins_records / g.eta > 0 ? h->bins_records / g.eta : 1;
+        const uint64_t bound = packed_bytes * 4;
+        const uint64_t chunks = (bound + per - 1) / per;
+        StageScope sc(h, RAMBO_STAGE_INSERT, s, (int)(2 * chunks));
+        for (uint64_t f0 = 0; f0 < bound; f0 += per) {
+            RAMBO_TRY(cudaMemsetAsync(h->d_bin_count, 0, (IB_MAX_BINS + 1) * 4, s));
+            RAMBO_TRY(launch_insert_binned(a, b, f0, f0 + per, h->sm_count, s));
+        }
+    } else {
+        if (a.mode == 3) a.mode = 2;  // the index is too large for regions that fit in L2
         StageScope sc(h, RAMBO_STAGE_INSERT, s, 1);
         RAMBO_TRY(launch_insert(a, h->sm_count, s));
     }
@@ -842,6 +866,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.expand_tc = 0;
     h->tune.host_fused_ctas_per_sm = 1;
     h->tune.insert_mode = 2;
+    h->tune.insert_bin_records = 0;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -863,6 +888,8 @@ int rambo_destroy(rambo_t *h) {
     cudaFree(h->d_stage);
     cudaFree(h->d_tab);
     cudaFree(h->d_ntab);
+    cudaFree(h->d_bins);
+    cudaFree(h->d_bin_count);
     for (auto &p : h->pending) {
         cudaEventDestroy(p.start);
         cudaEventDestroy(p.stop);
@@ -1273,6 +1300,36 @@ int rambo_get_tuning(const rambo_t *h, rambo_tuning_t *out) {
     return RAMBO_OK;
 }
 
+// The binned insert's record buffer, reserved when insert_mode 3 is chosen
+// (never during an insert, so that a captured insert allocates nothing) and
+// released when another mode is chosen.  The handle keeps its old buffer if
+// the new one cannot be had.
+static int reserve_bins(rambo_t *h, const rambo_tuning_t *t) {
+    if (t->insert_mode != 3) {
+        cudaFree(h->d_bins);
+        cudaFree(h->d_bin_count);
+        h->d_bins = nullptr;
+        h->d_bin_count = nullptr;
+        h->bins_records = 0;
+        return RAMBO_OK;
+    }
+    const uint64_t want = t->insert_bin_records ? t->insert_bin_records : (1ull << 28);
+    if (h->d_bins && h->bins_records == want) return RAMBO_OK;
+    unsigned long long *buf = nullptr;
+    uint32_t *cnt = nullptr;
+    if (cudaMalloc(&buf, want * 8) != cudaSuccess || cudaMalloc(&cnt, (IB_MAX_BINS + 1) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(buf);
+        return RAMBO_ENOMEM;
+    }
+    cudaFree(h->d_bins);
+    cudaFree(h->d_bin_count);
+    h->d_bins = buf;
+    h->d_bin_count = cnt;
+    h->bins_records = want;
+    return RAMBO_OK;
+}
+
 int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
     if (!h || !t) return RAMBO_EINVAL;
     if (t->probe_ctas_per_sm > 32 || t->expand_ctas_per_sm == 0 || t->expand_ctas_per_sm > 64 ||
@@ -1284,11 +1341,13 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22) ||
         (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
         t->host_direct > 1 || t->expand_tc > 1 || t->host_fused_ctas_per_sm > 32 ||
-        t->insert_mode > 2)
+        t->insert_mode > 3 || (t->insert_bin_records != 0 && t->insert_bin_records < 4096))
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
     RAMBO_TRY(sync_own_streams(h));
+    const int rc = reserve_bins(h, t);
+    if (rc) return rc;
     h->tune = *t;
     return apply_bytetab(h);
 }

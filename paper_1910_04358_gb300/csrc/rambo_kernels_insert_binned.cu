@@ -1,0 +1,223 @@
+// rambo_kernels_insert_binned.cu -- Algorithm 1's bit setting, binned by
+// index region so that its atomics hit L2.
+//
+// The direct insert ORs every probe's bits into a random line of the index:
+// once the index outgrows L2, nearly every atomic misses and costs a DRAM
+// read and write of the line.  Here a chunk of the batch's k-mers goes
+// through two passes:
+//   scatter  every probe (k-mer x, document d, position h_j(x)) becomes one
+//            8-byte record (h_j(x), d) appended to the bin of its index
+//            region; a CTA counts its tile's records per bin in shared
+//            memory, reserves each bin's share with one global atomicAdd and
+//            writes the records of a bin next to each other;
+//   apply    a persistent grid claims units of records in bin order, so all
+//            CTAs work inside one or two regions at a time and the regions
+//            stay in L2 while their records set bit r*B + phi_r(d) of group
+//            h_j(x) for every r (repetitions sharing a 64-bit word merged
+//            into one atomicOr, as the direct insert does).
+// Records past a bin's capacity set their bits during the scatter pass.  OR
+// is commutative and idempotent, so the index is bit-identical to the
+// direct insert's whatever the order.
+#include "rambo_insert_binned.cuh"
+
+namespace rgpu {
+namespace {
+
+constexpr int IB_THREADS = 256;
+constexpr uint32_t IB_UNIT = 2048;  // records per unit of the apply pass
+constexpr uint32_t NO_RANK = 0xffffffffu;
+
+// Sets the bits of one record: bit r*B + phi_r(d) of position group p for
+// every repetition r; `wide` merges repetitions that share a 64-bit word.
+__device__ __forceinline__ void or_record(const InsertArgs &a, uint64_t p, uint32_t d, bool wide) {
+    const uint64_t gbit = p * a.Gw * 32;  // first bit of the group
+    if (wide) {
+        unsigned long long *idx64 = reinterpret_cast<unsigned long long *>(a.index);
+        uint64_t cur = ~0ULL, bits = 0;
+        for (uint32_t r = 0; r < a.R; ++r) {
+            const uint64_t bb = gbit + r * a.B + __ldg(a.phi + (uint64_t)d * a.R + r);
+            if ((bb >> 6) != cur) {
+                if (bits) atomicOr(idx64 + cur, (unsigned long long)bits);
+                cur = bb >> 6;
+                bits = 0;
+            }
+            bits |= 1ull << (bb & 63);
+        }
+        if (bits) atomicOr(idx64 + cur, (unsigned long long)bits);
+    } else {
+        for (uint32_t r = 0; r < a.R; ++r) {
+            const uint64_t bb = gbit + r * a.B + __ldg(a.phi + (uint64_t)d * a.R + r);
+            atomicOr(a.index + (bb >> 5), 1u << (bb & 31));
+        }
+    }
+}
+
+// Scatter pass over [f0, f1) of the flat k-mer index: each CTA takes a
+// contiguous range in tiles of IB_THREADS k-mers (one per thread), up to ETA
+// probes of each per pass over the hash seeds.
+template <int ETA>
+__global__ void __launch_bounds__(IB_THREADS) k_insert_bin_scatter(InsertArgs a, BinnedInsert b, uint64_t f0,
+                                                                   uint64_t f1, bool wide) {
+    __shared__ uint32_t s_cnt[IB_MAX_BINS];
+    __shared__ uint32_t s_base[IB_MAX_BINS];
+    const uint64_t T = a.kcum[a.n];
+    const uint64_t e1 = f1 < T ? f1 : T;
+    if (f0 >= e1) return;  // the whole CTA
+    uint64_t per = (e1 - f0 + gridDim.x - 1) / gridDim.x;
+    per = (per + IB_THREADS - 1) / IB_THREADS * IB_THREADS;
+    const uint64_t c0 = f0 + (uint64_t)blockIdx.x * per;
+    if (c0 >= e1) return;  // the whole CTA
+    const uint64_t c1 = c0 + per < e1 ? c0 + per : e1;
+    for (uint32_t i = threadIdx.x; i < IB_MAX_BINS; i += IB_THREADS) s_cnt[i] = 0;
+    __syncthreads();
+
+    // document of this thread's first k-mer (largest i with kcum[i] <= g)
+    const uint64_t g_first = c0 + threadIdx.x < c1 ? c0 + threadIdx.x : c1 - 1;
+    uint64_t lo = 0, hi = a.n;
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a.kcum[mid] <= g_first) lo = mid;
+        else hi = mid;
+    }
+    const uint64_t item_first = lo;
+
+    for (uint32_t jb = 0; jb < a.eta; jb += ETA) {
+        uint64_t item = item_first;
+        for (uint64_t base = c0; base < c1; base += IB_THREADS) {
+            const uint64_t g = base + threadIdx.x;
+            bool val = g < c1;
+            uint32_t d = 0;
+            uint64_t c = 0;
+            if (val) {
+                while (a.kcum[item + 1] <= g) ++item;
+                d = a.doc_ids[item];
+                if (d >= a.K) {
+                    val = false;
+                } else {
+                    const uint64_t start = a.offsets[item] + a.base_shift + (g - a.kcum[item]);
+                    c = canonical_from_window(base_window(a.packed, a.packed_bytes, start), a.k);
+                }
+            }
+            const uint64_t km = mh_mix_key(c);
+            uint64_t rec[ETA];
+            uint32_t bin[ETA], rank[ETA];
+            // 1. this tile's records, ranked within their bins
+#pragma unroll
+            for (int e = 0; e < ETA; ++e) {
+                rank[e] = NO_RANK;
+                bin[e] = 0;
+                rec[e] = 0;
+                if (val && jb + e < a.eta) {
+                    const uint64_t h = mh_first_word(km, a.seed32 + jb + e);
+                    const uint64_t p = a.m_pow2 ? (h & (a.m - 1)) : (h % a.m);
+                    rec[e] = (p << IB_DOC_BITS) | d;
+                    bin[e] = (uint32_t)(p >> b.rshift);
+                    rank[e] = atomicAdd(&s_cnt[bin[e]], 1u);
+                }
+            }
+            __syncthreads();
+            // 2. each bin's share of the global bin, one atomic per bin
+            for (uint32_t i = threadIdx.x; i < b.nbins; i += IB_THREADS) {
+                const uint32_t n = s_cnt[i];
+                s_base[i] = n ? atomicAdd(b.count + i, n) : 0u;
+                s_cnt[i] = 0;
+            }
+            __syncthreads();
+            // 3. the records, or their bits when the bin is full
+#pragma unroll
+            for (int e = 0; e < ETA; ++e) {
+                if (rank[e] == NO_RANK) continue;
+                const uint64_t slot = (uint64_t)s_base[bin[e]] + rank[e];
+                if (slot < b.cap) b.buf[(uint64_t)bin[e] * b.cap + slot] = rec[e];
+                else or_record(a, rec[e] >> IB_DOC_BITS, d, wide);
+            }
+        }
+    }
+}
+
+// Apply pass: units of IB_UNIT records, claimed in bin order.
+__global__ void __launch_bounds__(IB_THREADS) k_insert_bin_apply(InsertArgs a, BinnedInsert b, bool wide) {
+    __shared__ uint32_t s_pre[IB_MAX_BINS + 1];  // units before bin i
+    __shared__ uint32_t s_unit;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (uint32_t i = 0; i < b.nbins; ++i) {
+            s_pre[i] = acc;
+            const uint64_t n = b.count[i] < b.cap ? b.count[i] : b.cap;
+            acc += (uint32_t)((n + IB_UNIT - 1) / IB_UNIT);
+        }
+        s_pre[b.nbins] = acc;
+    }
+    __syncthreads();
+    const uint32_t units = s_pre[b.nbins];
+    uint32_t *claim = b.count + IB_MAX_BINS;
+    while (true) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(claim, 1u);
+        __syncthreads();
+        const uint32_t u = s_unit;
+        __syncthreads();
+        if (u >= units) break;
+        // the bin holding unit u: s_pre[lo] <= u < s_pre[lo + 1]
+        uint32_t lo = 0, hi = b.nbins;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_pre[mid] <= u) lo = mid;
+            else hi = mid;
+        }
+        const uint64_t n = b.count[lo] < b.cap ? b.count[lo] : b.cap;
+        const uint64_t r0 = (uint64_t)(u - s_pre[lo]) * IB_UNIT;
+        const unsigned long long *src = b.buf + (uint64_t)lo * b.cap;
+        for (uint32_t k = threadIdx.x; k < IB_UNIT; k += IB_THREADS) {
+            const uint64_t r = r0 + k;
+            if (r < n) {
+                const unsigned long long rec = __ldcs(src + r);  // read once: do not keep in L2
+                or_record(a, rec >> IB_DOC_BITS, (uint32_t)(rec & ((1u << IB_DOC_BITS) - 1)), wide);
+            }
+        }
+    }
+}
+
+template <typename KernelT>
+int ib_blocks_per_sm(KernelT kernel) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, IB_THREADS, 0) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
+}
+
+template <int ETA>
+cudaError_t launch_scatter(const InsertArgs &a, const BinnedInsert &b, uint64_t f0, uint64_t f1, bool wide,
+                           int sm_count, cudaStream_t s) {
+    static int occ = ib_blocks_per_sm(k_insert_bin_scatter<ETA>);
+    k_insert_bin_scatter<ETA><<<sm_count * occ, IB_THREADS, 0, s>>>(a, b, f0, f1, wide);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t binned_insert_bins(uint64_t m, uint32_t group_bytes, uint32_t K, uint64_t region_bytes,
+                            uint32_t *rshift) {
+    if (m == 0 || group_bytes == 0 || m > (1ull << (64 - IB_DOC_BITS)) || K > (1u << IB_DOC_BITS)) return 0;
+    uint32_t sh = 0;
+    while (sh < 40 && ((uint64_t)group_bytes << (sh + 1)) <= region_bytes) ++sh;
+    const uint64_t bins = (m + (1ull << sh) - 1) >> sh;
+    if (bins > IB_MAX_BINS) return 0;
+    *rshift = sh;
+    return (uint32_t)bins;
+}
+
+cudaError_t launch_insert_binned(const InsertArgs &a, const BinnedInsert &b, uint64_t f0, uint64_t f1,
+                                 int sm_count, cudaStream_t s) {
+    // 64-bit words need the index (m * Gw words) to end on a 64-bit boundary
+    const bool wide = (a.m * a.Gw) % 2 == 0;
+    cudaError_t e;
+    if (a.eta == 1) e = launch_scatter<1>(a, b, f0, f1, wide, sm_count, s);
+    else if (a.eta == 2) e = launch_scatter<2>(a, b, f0, f1, wide, sm_count, s);
+    else e = launch_scatter<4>(a, b, f0, f1, wide, sm_count, s);
+    if (e != cudaSuccess) return e;
+    static int occ = ib_blocks_per_sm(k_insert_bin_apply);
+    k_insert_bin_apply<<<sm_count * occ, IB_THREADS, 0, s>>>(a, b, wide);
+    return cudaGetLastError();
+}
+
+}  // namespace rgpu

@@ -330,7 +330,7 @@ def test_argument_errors(rambo_lib):
     # tuning knobs out of range are refused and leave the tuning unchanged
     before = idx.get_tuning()
     for bad in (dict(query_path=3), dict(host_slots=0), dict(host_slots=5), dict(bin_rows=3),
-                dict(insert_mode=3), dict(expand_tc=2), dict(early_exit_segment=100)):
+                dict(insert_mode=4), dict(insert_bin_records=100), dict(expand_tc=2), dict(early_exit_segment=100)):
         with pytest.raises(rambo_lib.RamboError):
             idx.set_tuning(**bad)
     assert idx.get_tuning() == before
@@ -421,15 +421,18 @@ def test_insert_modes_give_identical_index(rambo_lib, K, B, R, m):
     corpus = synth.family_corpus(rng, p, n_seeds=max(1, K // 10), doc_len=500, sub_rate=0.02)
     o = oracle_index(p, corpus)
     base = None
-    for mode in (0, 1, 2):
+    # mode 3 (region-binned) with the default record buffer, and with one of
+    # 4096 records: many chunks, and bins that overflow into direct atomics;
+    # regions of 64 KiB so that the index spans several
+    for mode, recs in ((0, 0), (1, 0), (2, 0), (3, 0), (3, 4096)):
         idx = rambo_lib.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
-        idx.set_tuning(insert_mode=mode)
+        idx.set_tuning(insert_mode=mode, insert_bin_records=recs, bin_region_kib=64)
         idx.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
         bits = idx.copy_index()
         if base is None:
             base = bits
             assert_index_equal(idx, o, p)
-        assert np.array_equal(bits, base), mode
+        assert np.array_equal(bits, base), (mode, recs)
         idx.close()
 
 
