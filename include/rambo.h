@@ -370,7 +370,7 @@ typedef struct {
                                        /* probes are first written as 8-byte records   */
                                        /* per region, then applied region by region so */
                                        /* the atomics hit L2 -- for indexes of at most */
-                                       /* 128 regions, K <= 2^24 and m <= 2^40, else   */
+                                       /* 1024 regions, K <= 2^24 and m <= 2^40, else  */
                                        /* as 2.  Choosing 3 reserves the record buffer */
                                        /* (RAMBO_ENOMEM if it cannot be had)           */
     uint32_t insert_bin_records;       /* insert_mode 3: records the buffer holds      */

@@ -9,7 +9,7 @@ namespace rgpu {
 // Index regions the records are binned by: at most IB_MAX_BINS of them, each
 // 2^rshift position groups (about bin_region_kib of index bytes, a region
 // that stays in L2 while its records are applied).
-constexpr uint32_t IB_MAX_BINS = 128;
+constexpr uint32_t IB_MAX_BINS = 1024;
 
 // A record is (position << IB_DOC_BITS) | document: positions below 2^40,
 // documents below 2^24.

@@ -7,9 +7,9 @@
 // through two passes:
 //   scatter  every probe (k-mer x, document d, position h_j(x)) becomes one
 //            8-byte record (h_j(x), d) appended to the bin of its index
-//            region; a CTA counts its tile's records per bin in shared
-//            memory, reserves each bin's share with one global atomicAdd and
-//            writes the records of a bin next to each other;
+//            region; a CTA stages a tile of 4096 records in shared memory,
+//            counts them per bin, reserves each bin's share with one global
+//            atomicAdd and writes them out;
 //   apply    a persistent grid claims units of records in bin order, so all
 //            CTAs work inside one or two regions at a time and the regions
 //            stay in L2 while their records set bit r*B + phi_r(d) of group
@@ -53,22 +53,36 @@ __device__ __forceinline__ void or_record(const InsertArgs &a, uint64_t p, uint3
 }
 
 // Scatter pass over [f0, f1) of the flat k-mer index: each CTA takes a
-// contiguous range in tiles of IB_THREADS k-mers (one per thread), up to ETA
-// probes of each per pass over the hash seeds.
+// contiguous range in tiles of IB_TILE_RECORDS / ETA k-mers (every thread a
+// strided share), up to ETA probes of each per pass over the hash seeds.  A
+// tile's records are staged in shared memory with their bins and ranks, so
+// that a bin's share is reserved with one global atomic per tile even when
+// there are many bins.
+constexpr uint32_t IB_TILE_RECORDS = 4096;
+
+size_t scatter_smem() { return (size_t)IB_TILE_RECORDS * 16 + 2 * IB_MAX_BINS * 4; }
+
 template <int ETA>
 __global__ void __launch_bounds__(IB_THREADS) k_insert_bin_scatter(InsertArgs a, BinnedInsert b, uint64_t f0,
                                                                    uint64_t f1, bool wide) {
-    __shared__ uint32_t s_cnt[IB_MAX_BINS];
-    __shared__ uint32_t s_base[IB_MAX_BINS];
+    constexpr uint32_t TK = IB_TILE_RECORDS / ETA;  // k-mers per tile
+    constexpr uint32_t KPT = TK / IB_THREADS;       // k-mers per thread per tile
+    static_assert(KPT * IB_THREADS * ETA == IB_TILE_RECORDS, "tile of whole k-mer rounds");
+    extern __shared__ unsigned long long ib_smem[];
+    unsigned long long *s_rec = ib_smem;                                         // IB_TILE_RECORDS
+    uint32_t *s_bin = reinterpret_cast<uint32_t *>(s_rec + IB_TILE_RECORDS);     // bin, or NO_RANK
+    uint32_t *s_rank = s_bin + IB_TILE_RECORDS;                                  // rank within the bin
+    uint32_t *s_cnt = s_rank + IB_TILE_RECORDS;                                  // IB_MAX_BINS
+    uint32_t *s_base = s_cnt + IB_MAX_BINS;                                      // IB_MAX_BINS
     const uint64_t T = a.kcum[a.n];
     const uint64_t e1 = f1 < T ? f1 : T;
     if (f0 >= e1) return;  // the whole CTA
     uint64_t per = (e1 - f0 + gridDim.x - 1) / gridDim.x;
-    per = (per + IB_THREADS - 1) / IB_THREADS * IB_THREADS;
+    per = (per + TK - 1) / TK * TK;
     const uint64_t c0 = f0 + (uint64_t)blockIdx.x * per;
     if (c0 >= e1) return;  // the whole CTA
     const uint64_t c1 = c0 + per < e1 ? c0 + per : e1;
-    for (uint32_t i = threadIdx.x; i < IB_MAX_BINS; i += IB_THREADS) s_cnt[i] = 0;
+    for (uint32_t i = threadIdx.x; i < b.nbins; i += IB_THREADS) s_cnt[i] = 0;
     __syncthreads();
 
     // document of this thread's first k-mer (largest i with kcum[i] <= g)
@@ -83,36 +97,39 @@ __global__ void __launch_bounds__(IB_THREADS) k_insert_bin_scatter(InsertArgs a,
 
     for (uint32_t jb = 0; jb < a.eta; jb += ETA) {
         uint64_t item = item_first;
-        for (uint64_t base = c0; base < c1; base += IB_THREADS) {
-            const uint64_t g = base + threadIdx.x;
-            bool val = g < c1;
-            uint32_t d = 0;
-            uint64_t c = 0;
-            if (val) {
-                while (a.kcum[item + 1] <= g) ++item;
-                d = a.doc_ids[item];
-                if (d >= a.K) {
-                    val = false;
-                } else {
-                    const uint64_t start = a.offsets[item] + a.base_shift + (g - a.kcum[item]);
-                    c = canonical_from_window(base_window(a.packed, a.packed_bytes, start), a.k);
+        for (uint64_t base = c0; base < c1; base += TK) {
+            // 1. the tile's records, ranked within their bins (the k-mers a
+            //    thread takes increase, so its document walk only goes forward)
+            for (uint32_t kk = 0; kk < KPT; ++kk) {
+                const uint32_t j = kk * IB_THREADS + threadIdx.x;
+                const uint64_t g = base + j;
+                bool val = g < c1;
+                uint32_t d = 0;
+                uint64_t c = 0;
+                if (val) {
+                    while (a.kcum[item + 1] <= g) ++item;
+                    d = a.doc_ids[item];
+                    if (d >= a.K) {
+                        val = false;
+                    } else {
+                        const uint64_t start = a.offsets[item] + a.base_shift + (g - a.kcum[item]);
+                        c = canonical_from_window(base_window(a.packed, a.packed_bytes, start), a.k);
+                    }
                 }
-            }
-            const uint64_t km = mh_mix_key(c);
-            uint64_t rec[ETA];
-            uint32_t bin[ETA], rank[ETA];
-            // 1. this tile's records, ranked within their bins
+                const uint64_t km = mh_mix_key(c);
 #pragma unroll
-            for (int e = 0; e < ETA; ++e) {
-                rank[e] = NO_RANK;
-                bin[e] = 0;
-                rec[e] = 0;
-                if (val && jb + e < a.eta) {
-                    const uint64_t h = mh_first_word(km, a.seed32 + jb + e);
-                    const uint64_t p = a.m_pow2 ? (h & (a.m - 1)) : (h % a.m);
-                    rec[e] = (p << IB_DOC_BITS) | d;
-                    bin[e] = (uint32_t)(p >> b.rshift);
-                    rank[e] = atomicAdd(&s_cnt[bin[e]], 1u);
+                for (int e = 0; e < ETA; ++e) {
+                    const uint32_t slot = j * ETA + e;
+                    if (val && jb + e < a.eta) {
+                        const uint64_t h = mh_first_word(km, a.seed32 + jb + e);
+                        const uint64_t p = a.m_pow2 ? (h & (a.m - 1)) : (h % a.m);
+                        const uint32_t bin = (uint32_t)(p >> b.rshift);
+                        s_rec[slot] = (p << IB_DOC_BITS) | d;
+                        s_bin[slot] = bin;
+                        s_rank[slot] = atomicAdd(&s_cnt[bin], 1u);
+                    } else {
+                        s_bin[slot] = NO_RANK;
+                    }
                 }
             }
             __syncthreads();
@@ -124,13 +141,15 @@ __global__ void __launch_bounds__(IB_THREADS) k_insert_bin_scatter(InsertArgs a,
             }
             __syncthreads();
             // 3. the records, or their bits when the bin is full
-#pragma unroll
-            for (int e = 0; e < ETA; ++e) {
-                if (rank[e] == NO_RANK) continue;
-                const uint64_t slot = (uint64_t)s_base[bin[e]] + rank[e];
-                if (slot < b.cap) b.buf[(uint64_t)bin[e] * b.cap + slot] = rec[e];
-                else or_record(a, rec[e] >> IB_DOC_BITS, d, wide);
+            for (uint32_t slot = threadIdx.x; slot < IB_TILE_RECORDS; slot += IB_THREADS) {
+                const uint32_t bin = s_bin[slot];
+                if (bin == NO_RANK) continue;
+                const unsigned long long rec = s_rec[slot];
+                const uint64_t at = (uint64_t)s_base[bin] + s_rank[slot];
+                if (at < b.cap) b.buf[(uint64_t)bin * b.cap + at] = rec;
+                else or_record(a, rec >> IB_DOC_BITS, (uint32_t)(rec & ((1u << IB_DOC_BITS) - 1)), wide);
             }
+            __syncthreads();  // the staging is the next tile's
         }
     }
 }
@@ -139,14 +158,31 @@ __global__ void __launch_bounds__(IB_THREADS) k_insert_bin_scatter(InsertArgs a,
 __global__ void __launch_bounds__(IB_THREADS) k_insert_bin_apply(InsertArgs a, BinnedInsert b, bool wide) {
     __shared__ uint32_t s_pre[IB_MAX_BINS + 1];  // units before bin i
     __shared__ uint32_t s_unit;
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (uint32_t i = 0; i < b.nbins; ++i) {
-            s_pre[i] = acc;
-            const uint64_t n = b.count[i] < b.cap ? b.count[i] : b.cap;
-            acc += (uint32_t)((n + IB_UNIT - 1) / IB_UNIT);
+    // units per bin, then their exclusive prefix (warp 0: lane l sums bins
+    // l*PER .. l*PER + PER - 1, a warp scan, then each lane writes its run)
+    for (uint32_t i = threadIdx.x; i < b.nbins; i += IB_THREADS) {
+        const uint64_t n = b.count[i] < b.cap ? b.count[i] : b.cap;
+        s_pre[i] = (uint32_t)((n + IB_UNIT - 1) / IB_UNIT);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr uint32_t PER = IB_MAX_BINS / 32;
+        const uint32_t lane = threadIdx.x, i0 = lane * PER;
+        uint32_t sum = 0;
+        for (uint32_t i = i0; i < i0 + PER; ++i) sum += i < b.nbins ? s_pre[i] : 0u;
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= (uint32_t)off) incl += o;
         }
-        s_pre[b.nbins] = acc;
+        uint32_t run = incl - sum;
+        for (uint32_t i = i0; i < i0 + PER && i < b.nbins; ++i) {
+            const uint32_t u = s_pre[i];
+            s_pre[i] = run;
+            run += u;
+        }
+        if (lane == 31) s_pre[b.nbins] = incl;
     }
     __syncthreads();
     const uint32_t units = s_pre[b.nbins];
@@ -188,8 +224,21 @@ int ib_blocks_per_sm(KernelT kernel) {
 template <int ETA>
 cudaError_t launch_scatter(const InsertArgs &a, const BinnedInsert &b, uint64_t f0, uint64_t f1, bool wide,
                            int sm_count, cudaStream_t s) {
-    static int occ = ib_blocks_per_sm(k_insert_bin_scatter<ETA>);
-    k_insert_bin_scatter<ETA><<<sm_count * occ, IB_THREADS, 0, s>>>(a, b, f0, f1, wide);
+    const size_t smem = scatter_smem();
+    static int occ = [smem] {
+        int n = 0;
+        if (cudaFuncSetAttribute(k_insert_bin_scatter<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_insert_bin_scatter<ETA>, IB_THREADS, smem) !=
+                cudaSuccess ||
+            n < 1)
+            n = 1;
+        return n;
+    }();
+    cudaError_t e = cudaFuncSetAttribute(k_insert_bin_scatter<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_insert_bin_scatter<ETA><<<sm_count * occ, IB_THREADS, smem, s>>>(a, b, f0, f1, wide);
     return cudaGetLastError();
 }
 

@@ -423,16 +423,18 @@ def test_insert_modes_give_identical_index(rambo_lib, K, B, R, m):
     base = None
     # mode 3 (region-binned) with the default record buffer, and with one of
     # 4096 records: many chunks, and bins that overflow into direct atomics;
-    # regions of 64 KiB so that the index spans several
-    for mode, recs in ((0, 0), (1, 0), (2, 0), (3, 0), (3, 4096)):
+    # regions of 64 KiB so that the index spans several, or of 1 KiB so that
+    # it spans hundreds
+    for mode, recs, kib in ((0, 0, 64), (1, 0, 64), (2, 0, 64), (3, 0, 64), (3, 4096, 64), (3, 0, 1),
+                            (3, 8192, 1)):
         idx = rambo_lib.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
-        idx.set_tuning(insert_mode=mode, insert_bin_records=recs, bin_region_kib=64)
+        idx.set_tuning(insert_mode=mode, insert_bin_records=recs, bin_region_kib=kib)
         idx.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
         bits = idx.copy_index()
         if base is None:
             base = bits
             assert_index_equal(idx, o, p)
-        assert np.array_equal(bits, base), (mode, recs)
+        assert np.array_equal(bits, base), (mode, recs, kib)
         idx.close()
 
 
