@@ -376,6 +376,10 @@ typedef struct {
     uint32_t insert_bin_records;       /* insert_mode 3: records the buffer holds      */
                                        /* (8 bytes each; 0 = 2^28, else >= 4096); a    */
                                        /* batch is applied in chunks that fill it      */
+    uint32_t fused_async;              /* query_path 1, 16-byte groups, eta <= 2: 1 =  */
+                                       /* the probes' gathers land in shared memory    */
+                                       /* (cp.async) instead of registers, so the      */
+                                       /* launch needs fewer registers (default 0)     */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

@@ -33,6 +33,9 @@ KNOBS = (
     ("use_byte_table", (0, 1)),
     ("smem_docbits", (0, 1)),
     ("expand_ctas_per_sm", (2, 4, 8, 16, 32)),
+    # staged gathers before the fused grid: they pay off at a smaller grid
+    # that leaves room for the k-mer branch beside it
+    ("fused_async", (0, 1)),
     ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
     ("kmer_probe_ctas_per_sm", (0, 1, 2, 3, 4)),
     ("bin_region_kib", (16384, 32768, 65536)),
@@ -81,7 +84,7 @@ def _descend(idx, run, outputs, ref, start, knobs, reps, info, trials, verbose):
     trials.append({"tuning": dict(start), "ms": best_ms})
     path = effective_path(start, info)
     for knob, values in knobs:
-        if knob in ("fused_tile_kmers", "fused_short_max") and path != 1:
+        if knob in ("fused_tile_kmers", "fused_short_max", "fused_async") and path != 1:
             continue
         if knob in ("bin_region_kib", "bin_rows") and path != 2:
             continue

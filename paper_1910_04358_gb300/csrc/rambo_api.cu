@@ -413,6 +413,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         qs.user_bases = packed_bytes * 4;
         qs.early_exit = h->tune.early_exit;
         qs.segment = h->tune.early_exit_segment;
+        qs.async = h->tune.fused_async;
         qs.probed = h->d_probed;
         {
             StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
@@ -867,6 +868,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.host_fused_ctas_per_sm = 1;
     h->tune.insert_mode = 2;
     h->tune.insert_bin_records = 0;
+    h->tune.fused_async = 0;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -1341,7 +1343,8 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22) ||
         (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
         t->host_direct > 1 || t->expand_tc > 1 || t->host_fused_ctas_per_sm > 32 ||
-        t->insert_mode > 3 || (t->insert_bin_records != 0 && t->insert_bin_records < 4096))
+        t->insert_mode > 3 || (t->insert_bin_records != 0 && t->insert_bin_records < 4096) ||
+        t->fused_async > 1)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

@@ -288,6 +288,7 @@ struct FusedQueues {
     uint32_t early_exit;     // 1: skip the rest of a query once a repetition row is empty
     uint32_t segment;        // early exit: k-mers between checks (multiple of 128)
     unsigned long long *probed;  // early exit: k-mers actually probed (or null)
+    uint32_t async;          // 1: one-lane 16-byte groups gathered into shared memory (cp.async)
 };
 bool fused_supported(const Geometry &g);
 // Region-binned probing of a sequence batch (query path 2, groups of at most

@@ -84,13 +84,34 @@ __global__ void k_fused_prep(FusedArgs f) {
     }
 }
 
+// 16-byte copy from global to shared memory that does not pass through
+// registers (caching in L2 only), and the wait for this thread's copies.
+__device__ __forceinline__ void cp_async16(uint4 *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Rounds of loads a lane keeps in flight, and (ASYNC) the shared-memory
+// staging a warp needs for them: one 16-byte slot per lane, round and probe.
+template <int LPG>
+__host__ __device__ constexpr int fused_rif() { return LPG == 1 ? 8 : 4; }
+template <int ETA>
+__host__ __device__ constexpr size_t fused_stage_bytes() { return (size_t)(FUSED_THREADS / 32) * fused_rif<1>() * ETA * 32 * 16; }
+
 // AND of the groups of k-mers [k0, k1) of one query, per lane slice (every
-// lane of the warp works on the same query).
-template <int SW, int LPG, int ETA>
+// lane of the warp works on the same query).  ASYNC (one lane per 16-byte
+// group): the gathers land in the warp's shared-memory `stage` through
+// cp.async instead of registers, so a lane holds no load data in flight.
+template <int SW, int LPG, int ETA, bool ASYNC>
 __device__ __forceinline__ Slice<SW> fused_probe_range(const ProbeArgs &a, uint64_t start,
                                                         uint64_t k0, uint64_t k1, int lane,
-                                                        uint32_t word0) {
-    constexpr int RIF = LPG == 1 ? 8 : 4;  // rounds whose loads are in flight together
+                                                        uint32_t word0, uint4 *stage) {
+    static_assert(!ASYNC || (LPG == 1 && SW == 4), "staged gathers: one lane per 16-byte group");
+    constexpr int RIF = fused_rif<LPG>();  // rounds whose loads are in flight together
     constexpr int NT = LPG >= RIF ? 1 : RIF / LPG;
     constexpr int KPR = 32 / LPG;
     constexpr int ROUNDS = NT * LPG;
@@ -118,6 +139,32 @@ __device__ __forceinline__ Slice<SW> fused_probe_range(const ProbeArgs &a, uint6
             }
 #pragma unroll
             for (int rg = 0; rg < ROUNDS; rg += RIF) {
+                if constexpr (ASYNC) {
+                    // each lane gathers its own k-mers' groups (LPG == 1)
+                    uint32_t live = 0;
+#pragma unroll
+                    for (int rr = 0; rr < RIF; ++rr) {
+                        const int t = rg + rr;
+#pragma unroll
+                        for (int e = 0; e < ETA; ++e)
+                            if (val[t]) {
+                                cp_async16(stage + (rr * ETA + e) * 32 + lane,
+                                           a.index + (uint64_t)pos[t][e] * a.Gw + word0);
+                                live |= 1u << (rr * ETA + e);
+                            }
+                    }
+                    cp_async_wait_all();
+#pragma unroll
+                    for (int i = 0; i < RIF * ETA; ++i)
+                        if (live & (1u << i)) {
+                            const uint4 v = stage[i * 32 + lane];
+                            accv.w[0] &= v.x;
+                            accv.w[1] &= v.y;
+                            accv.w[2] &= v.z;
+                            accv.w[3] &= v.w;
+                        }
+                    continue;
+                }
                 Slice<SW> v[RIF][ETA];
 #pragma unroll
                 for (int rr = 0; rr < RIF; ++rr) {
@@ -147,16 +194,19 @@ __device__ __forceinline__ Slice<SW> fused_probe_range(const ProbeArgs &a, uint6
     return accv;
 }
 
-template <int SW, int LPG, int ETA, int C>
+template <int SW, int LPG, int ETA, int C, bool ASYNC>
 // three resident blocks per SM fit without spills for groups read by 4+
-// lanes; one-lane groups keep 16 loads per lane in flight at two
-__global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(FusedArgs f) {
+// lanes; one-lane groups keep 16 loads per lane in flight at two (in
+// registers) or at three (staged in shared memory)
+__global__ void __launch_bounds__(FUSED_THREADS, (LPG >= 4 || ASYNC) ? 3 : 2) k_fused(FusedArgs f) {
     __shared__ uint32_t bm_smem[FUSED_THREADS / 32][128];
     __shared__ uint32_t list_smem[FUSED_THREADS / 32][EXPAND_LIST_MAX];
+    extern __shared__ uint4 fused_stage[];  // ASYNC: fused_stage_bytes<ETA>()
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     uint32_t *bm = bm_smem[wib];
     uint32_t *list = list_smem[wib];
+    uint4 *stage = fused_stage + (size_t)wib * fused_rif<1>() * ETA * 32;
     const int sub = lane / LPG;
     const uint32_t word0 = (lane % LPG) * SW;
     const uint32_t n_short = f.counters[0];
@@ -198,7 +248,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(Fused
             const uint64_t seg = f.early_exit ? f.segment : (k1 > k0 ? k1 - k0 : 1);
             for (uint64_t a0 = k0; a0 < k1; a0 += seg) {
                 const uint64_t a1 = a0 + seg < k1 ? a0 + seg : k1;
-                slice_and(s, fused_probe_range<SW, LPG, ETA>(f.p, start, a0, a1, lane, word0));
+                slice_and(s, fused_probe_range<SW, LPG, ETA, ASYNC>(f.p, start, a0, a1, lane, word0, stage));
                 if (!f.early_exit) continue;
                 if (lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(a1 - a0));
                 if (a1 >= k1) break;
@@ -240,7 +290,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(Fused
         const uint64_t seg = f.early_exit ? f.segment : (nk ? nk : 1);
         for (uint64_t k0 = 0; k0 < nk; k0 += seg) {
             const uint64_t k1 = k0 + seg < nk ? k0 + seg : nk;
-            slice_and(sl, fused_probe_range<SW, LPG, ETA>(f.p, start, k0, k1, lane, word0));
+            slice_and(sl, fused_probe_range<SW, LPG, ETA, ASYNC>(f.p, start, k0, k1, lane, word0, stage));
             if (!f.early_exit) continue;
             if (lane == 0 && f.probed) atomicAdd(f.probed, (unsigned long long)(k1 - k0));
             if (k1 >= nk) break;
@@ -263,26 +313,40 @@ __global__ void __launch_bounds__(FUSED_THREADS, LPG >= 4 ? 3 : 2) k_fused(Fused
 
 }  // namespace
 
-template <int SW, int LPG, int ETA, int C>
+template <int SW, int LPG, int ETA, int C, bool ASYNC>
 cudaError_t launch_fused_t(const FusedArgs &f, int grid_override, int sm_count, cudaStream_t s) {
-    static int occ = blocks_per_sm(k_fused<SW, LPG, ETA, C>, FUSED_THREADS, 0);
+    const size_t smem = ASYNC ? fused_stage_bytes<ETA>() : 0;
+    if (ASYNC) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused<SW, LPG, ETA, C, ASYNC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    static int occ = blocks_per_sm(k_fused<SW, LPG, ETA, C, ASYNC>, FUSED_THREADS, smem);
     const int grid = grid_override > 0 ? grid_override : sm_count * occ;
-    k_fused<SW, LPG, ETA, C><<<grid, FUSED_THREADS, 0, s>>>(f);
+    k_fused<SW, LPG, ETA, C, ASYNC><<<grid, FUSED_THREADS, smem, s>>>(f);
     return cudaGetLastError();
 }
 
-template <int SW, int LPG, int ETA>
+template <int SW, int LPG, int ETA, bool ASYNC>
 cudaError_t launch_fused_c(const FusedArgs &f, int go, int sm, cudaStream_t s) {
-    if (f.e.W > 64) return launch_fused_t<SW, LPG, ETA, 4>(f, go, sm, s);
-    return launch_fused_t<SW, LPG, ETA, 1>(f, go, sm, s);
+    if (f.e.W > 64) return launch_fused_t<SW, LPG, ETA, 4, ASYNC>(f, go, sm, s);
+    return launch_fused_t<SW, LPG, ETA, 1, ASYNC>(f, go, sm, s);
 }
 
 template <int SW, int LPG>
-cudaError_t launch_fused_e(const FusedArgs &f, int go, int sm, cudaStream_t s) {
+cudaError_t launch_fused_e(const FusedArgs &f, int go, int sm, cudaStream_t s, bool async) {
+    // staged gathers for one lane per 16-byte group and at most two probes a
+    // round (the staging of four would take 128 KB per block)
+    if constexpr (SW == 4 && LPG == 1) {
+        if (async && f.p.eta <= 2) {
+            if (f.p.eta == 1) return launch_fused_c<SW, LPG, 1, true>(f, go, sm, s);
+            return launch_fused_c<SW, LPG, 2, true>(f, go, sm, s);
+        }
+    }
     switch (f.p.eta) {
-        case 1: return launch_fused_c<SW, LPG, 1>(f, go, sm, s);
-        case 2: return launch_fused_c<SW, LPG, 2>(f, go, sm, s);
-        default: return launch_fused_c<SW, LPG, 4>(f, go, sm, s);
+        case 1: return launch_fused_c<SW, LPG, 1, false>(f, go, sm, s);
+        case 2: return launch_fused_c<SW, LPG, 2, false>(f, go, sm, s);
+        default: return launch_fused_c<SW, LPG, 4, false>(f, go, sm, s);
     }
 }
 
@@ -309,15 +373,16 @@ cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry
     if (p.n == 0) return cudaSuccess;
     k_fused_prep<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(f);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    if (g.SW == 1) return launch_fused_e<1, 1>(f, grid_override, sm_count, s);
-    if (g.SW == 2) return launch_fused_e<2, 1>(f, grid_override, sm_count, s);
+    const bool as = qs.async != 0;
+    if (g.SW == 1) return launch_fused_e<1, 1>(f, grid_override, sm_count, s, as);
+    if (g.SW == 2) return launch_fused_e<2, 1>(f, grid_override, sm_count, s, as);
     switch (g.LPG) {
-        case 1: return launch_fused_e<4, 1>(f, grid_override, sm_count, s);
-        case 2: return launch_fused_e<4, 2>(f, grid_override, sm_count, s);
-        case 4: return launch_fused_e<4, 4>(f, grid_override, sm_count, s);
-        case 8: return launch_fused_e<4, 8>(f, grid_override, sm_count, s);
-        case 16: return launch_fused_e<4, 16>(f, grid_override, sm_count, s);
-        case 32: return launch_fused_e<4, 32>(f, grid_override, sm_count, s);
+        case 1: return launch_fused_e<4, 1>(f, grid_override, sm_count, s, as);
+        case 2: return launch_fused_e<4, 2>(f, grid_override, sm_count, s, as);
+        case 4: return launch_fused_e<4, 4>(f, grid_override, sm_count, s, as);
+        case 8: return launch_fused_e<4, 8>(f, grid_override, sm_count, s, as);
+        case 16: return launch_fused_e<4, 16>(f, grid_override, sm_count, s, as);
+        case 32: return launch_fused_e<4, 32>(f, grid_override, sm_count, s, as);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -190,6 +190,28 @@ def test_many_documents_several_answer_chunks(rambo_lib, path):
     assert (pops[-5:] == p.K).all() and (pops[:200] < p.K).all()
 
 
+@pytest.mark.parametrize("eta", [1, 2, 3])
+def test_fused_staged_gathers(rambo_lib, eta):
+    # 16-byte groups (one lane per group): the fused launch can gather through
+    # shared memory (cp.async) instead of registers; eta 3 keeps the register
+    # gathers.  Tiles, short-query thresholds and early exit vary around it.
+    p = synth.Params(K=300, B=32, R=4, m=1 << 14, eta=eta, k=31, seed=8)
+    rng = np.random.default_rng(eta)
+    corpus = synth.family_corpus(rng, p, n_seeds=20, doc_len=600, sub_rate=0.02)
+    q = synth.sample_queries(rng, corpus, rng.integers(20, 900, size=300), 0.6)
+    o = oracle_index(p, corpus)
+    want = o.query_seqs(q.packed, q.offsets)
+    idx = gpu_index(rambo_lib, p, corpus)
+    for st in (dict(fused_async=1, fused_tile_kmers=1024, fused_short_max=1024),
+               dict(fused_async=1, fused_tile_kmers=64, fused_short_max=40),
+               dict(fused_async=1, fused_tile_kmers=256, fused_short_max=0, probe_ctas_per_sm=2),
+               dict(fused_async=1, fused_tile_kmers=128, fused_short_max=300, early_exit=1,
+                    early_exit_segment=128),
+               dict(fused_async=0, fused_tile_kmers=64, fused_short_max=40)):
+        idx.set_tuning(query_path=1, **st)
+        assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want), st
+
+
 def test_tuning_knobs_do_not_change_results(rambo_lib):
     p = synth.Params(K=300, B=40, R=4, m=1 << 13, eta=2, k=31, seed=4)
     rng = np.random.default_rng(77)
@@ -330,7 +352,7 @@ def test_argument_errors(rambo_lib):
     # tuning knobs out of range are refused and leave the tuning unchanged
     before = idx.get_tuning()
     for bad in (dict(query_path=3), dict(host_slots=0), dict(host_slots=5), dict(bin_rows=3),
-                dict(insert_mode=4), dict(insert_bin_records=100), dict(expand_tc=2), dict(early_exit_segment=100)):
+                dict(insert_mode=4), dict(insert_bin_records=100), dict(fused_async=2), dict(expand_tc=2), dict(early_exit_segment=100)):
         with pytest.raises(rambo_lib.RamboError):
             idx.set_tuning(**bad)
     assert idx.get_tuning() == before
