@@ -380,6 +380,8 @@ typedef struct {
                                        /* the probes' gathers land in shared memory    */
                                        /* (cp.async) instead of registers, so the      */
                                        /* launch needs fewer registers (default 0)     */
+    uint32_t kmer_async;               /* the same for the single k-mer probe (16-byte */
+                                       /* groups, eta <= 2; default 0)                 */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

@@ -37,6 +37,7 @@ KNOBS = (
     # that leaves room for the k-mer branch beside it
     ("fused_async", (0, 1)),
     ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
+    ("kmer_async", (0, 1)),
     ("kmer_probe_ctas_per_sm", (0, 1, 2, 3, 4)),
     ("bin_region_kib", (16384, 32768, 65536)),
     ("bin_rows", (1, 2, 4, 8)),

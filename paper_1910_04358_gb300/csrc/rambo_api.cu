@@ -486,7 +486,7 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
     a.min_chunk = h->tune.probe_min_kmers_per_warp;
     {
         StageScope sc(h, RAMBO_STAGE_PROBE_KMERS, s, 1);
-        RAMBO_TRY(launch_probe_kmers(a, g, kmer_probe_grid(h), s));
+        RAMBO_TRY(launch_probe_kmers(a, g, kmer_probe_grid(h), s, h->tune.kmer_async != 0));
     }
     ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                      h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
@@ -869,6 +869,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.insert_mode = 2;
     h->tune.insert_bin_records = 0;
     h->tune.fused_async = 0;
+    h->tune.kmer_async = 0;
     if ((rc = apply_bytetab(h))) return fail(rc);
     *out = h;
     return RAMBO_OK;
@@ -1344,7 +1345,7 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
         t->host_direct > 1 || t->expand_tc > 1 || t->host_fused_ctas_per_sm > 32 ||
         t->insert_mode > 3 || (t->insert_bin_records != 0 && t->insert_bin_records < 4096) ||
-        t->fused_async > 1)
+        t->fused_async > 1 || t->kmer_async > 1)
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;

@@ -275,7 +275,9 @@ cudaError_t launch_fold(const uint32_t *old_index, uint32_t old_gw, uint32_t *ne
                         const uint32_t *old_db, uint32_t *new_db, uint32_t W, int sm_count,
                         cudaStream_t s);
 cudaError_t launch_probe_seqs(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
-cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
+// staged: one-lane 16-byte groups and eta <= 2 gather into shared memory (cp.async)
+cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s,
+                               bool staged);
 // Work queues of the persistent fused query (workspace arrays).
 struct FusedQueues {
     uint32_t *counters;      // 4 words, zeroed by the launcher

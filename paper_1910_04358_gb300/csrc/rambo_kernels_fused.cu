@@ -84,17 +84,6 @@ __global__ void k_fused_prep(FusedArgs f) {
     }
 }
 
-// 16-byte copy from global to shared memory that does not pass through
-// registers (caching in L2 only), and the wait for this thread's copies.
-__device__ __forceinline__ void cp_async16(uint4 *smem, const void *gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 // Rounds of loads a lane keeps in flight, and (ASYNC) the shared-memory
 // staging a warp needs for them: one 16-byte slot per lane, round and probe.
 template <int LPG>

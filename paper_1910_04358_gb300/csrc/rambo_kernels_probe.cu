@@ -123,10 +123,18 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_seqs(ProbeArgs a) {
 
 // ---------------------------------------------------------------------------
 // probe: single k-mers (each k-mer is its own query; no cross-k-mer AND, so
-// the bucket mask is stored directly).
-template <int SW, int LPG, int ETA>
-__global__ void __launch_bounds__(PROBE_THREADS) k_probe_kmers(ProbeArgs a) {
-    constexpr int RIF = LPG == 1 ? 8 : 4;  // rounds whose loads are in flight together
+// the bucket mask is stored directly).  STAGED (one lane per 16-byte group):
+// the gathers land in the warp's shared-memory stage through cp.async, so a
+// lane holds no load data in flight and the kernel fits beside other work.
+constexpr int KMER_RIF1 = 8;  // rounds in flight for one-lane groups
+template <int ETA>
+constexpr size_t kmer_stage_bytes() { return (size_t)(PROBE_THREADS / 32) * KMER_RIF1 * ETA * 32 * 16; }
+
+template <int SW, int LPG, int ETA, bool STAGED = false>
+__global__ void __launch_bounds__(PROBE_THREADS, STAGED ? 3 : 1) k_probe_kmers(ProbeArgs a) {
+    static_assert(!STAGED || (LPG == 1 && SW == 4), "staged gathers: one lane per 16-byte group");
+    extern __shared__ uint4 kmer_stage[];
+    constexpr int RIF = LPG == 1 ? KMER_RIF1 : 4;  // rounds whose loads are in flight together
     constexpr int NT = LPG >= RIF ? 1 : RIF / LPG;
     constexpr int KPR = 32 / LPG;
     constexpr int ROUNDS = NT * LPG;
@@ -167,6 +175,42 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_kmers(ProbeArgs a) {
             }
 #pragma unroll
             for (int rg = 0; rg < ROUNDS; rg += RIF) {
+                if constexpr (STAGED) {
+                    // each lane gathers its own k-mers' groups (LPG == 1)
+                    uint4 *stage = kmer_stage + (size_t)(threadIdx.x >> 5) * RIF * ETA * 32;
+#pragma unroll
+                    for (int rr = 0; rr < RIF; ++rr)
+                        if (val[rg + rr])
+#pragma unroll
+                            for (int e = 0; e < ETA; ++e)
+                                cp_async16(stage + (rr * ETA + e) * 32 + lane,
+                                           a.index + (uint64_t)pos[rg + rr][e] * a.Gw + word0);
+                    cp_async_wait_all();
+#pragma unroll
+                    for (int rr = 0; rr < RIF; ++rr) {
+                        if (!val[rg + rr]) continue;
+                        const uint64_t g = base + (uint64_t)(rg + rr) * 32 + lane;
+                        uint4 x = stage[(rr * ETA) * 32 + lane];
+#pragma unroll
+                        for (int e = 1; e < ETA; ++e) {
+                            const uint4 y = stage[(rr * ETA + e) * 32 + lane];
+                            x.x &= y.x;
+                            x.y &= y.y;
+                            x.z &= y.z;
+                            x.w &= y.w;
+                        }
+                        uint32_t *p = a.acc + g * a.Gw + word0;
+                        if (jb == 0) {
+                            *reinterpret_cast<uint4 *>(p) = x;
+                        } else {
+                            atomicAnd(p, x.x);
+                            atomicAnd(p + 1, x.y);
+                            atomicAnd(p + 2, x.z);
+                            atomicAnd(p + 3, x.w);
+                        }
+                    }
+                    continue;
+                }
                 Slice<SW> v[RIF][ETA];
                 bool vs[RIF];
 #pragma unroll
@@ -204,10 +248,24 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_kmers(ProbeArgs a) {
     }
 }
 
+template <int ETA>
+cudaError_t launch_kmers_staged(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s) {
+    const size_t smem = kmer_stage_bytes<ETA>();
+    cudaError_t e = cudaFuncSetAttribute(k_probe_kmers<4, 1, ETA, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    static int occ = blocks_per_sm(k_probe_kmers<4, 1, ETA, true>, PROBE_THREADS, smem);
+    const dim3 grid(sm_count > 0 ? sm_count * occ : -sm_count, g.chunks);
+    k_probe_kmers<4, 1, ETA, true><<<grid, PROBE_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int SW, int LPG, int ETA>
 cudaError_t launch_probe_t(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s,
-                           bool kmers) {
+                           bool kmers, bool staged) {
     // sm_count > 0: SMs x occupancy maximum; sm_count < 0: -sm_count CTAs
+    if constexpr (SW == 4 && LPG == 1 && ETA <= 2)
+        if (kmers && staged) return launch_kmers_staged<ETA>(a, g, sm_count, s);
     dim3 grid, block(PROBE_THREADS);
     if (kmers) {
         static int occ = blocks_per_sm(k_probe_kmers<SW, LPG, ETA>, PROBE_THREADS, 0);
@@ -222,25 +280,26 @@ cudaError_t launch_probe_t(const ProbeArgs &a, const Geometry &g, int sm_count, 
 }
 
 template <int SW, int LPG>
-cudaError_t launch_probe_eta(const ProbeArgs &a, const Geometry &g, int sm, cudaStream_t s, bool km) {
+cudaError_t launch_probe_eta(const ProbeArgs &a, const Geometry &g, int sm, cudaStream_t s, bool km,
+                             bool st) {
     switch (g.eta) {
-        case 1: return launch_probe_t<SW, LPG, 1>(a, g, sm, s, km);
-        case 2: return launch_probe_t<SW, LPG, 2>(a, g, sm, s, km);
-        case 3: return launch_probe_t<SW, LPG, 3>(a, g, sm, s, km);
-        default: return launch_probe_t<SW, LPG, 4>(a, g, sm, s, km);
+        case 1: return launch_probe_t<SW, LPG, 1>(a, g, sm, s, km, st);
+        case 2: return launch_probe_t<SW, LPG, 2>(a, g, sm, s, km, st);
+        case 3: return launch_probe_t<SW, LPG, 3>(a, g, sm, s, km, st);
+        default: return launch_probe_t<SW, LPG, 4>(a, g, sm, s, km, st);
     }
 }
 
-cudaError_t launch_probe(const ProbeArgs &a, const Geometry &g, int sm, cudaStream_t s, bool km) {
-    if (g.SW == 1) return launch_probe_eta<1, 1>(a, g, sm, s, km);
-    if (g.SW == 2) return launch_probe_eta<2, 1>(a, g, sm, s, km);
+cudaError_t launch_probe(const ProbeArgs &a, const Geometry &g, int sm, cudaStream_t s, bool km, bool st) {
+    if (g.SW == 1) return launch_probe_eta<1, 1>(a, g, sm, s, km, st);
+    if (g.SW == 2) return launch_probe_eta<2, 1>(a, g, sm, s, km, st);
     switch (g.LPG) {
-        case 1: return launch_probe_eta<4, 1>(a, g, sm, s, km);
-        case 2: return launch_probe_eta<4, 2>(a, g, sm, s, km);
-        case 4: return launch_probe_eta<4, 4>(a, g, sm, s, km);
-        case 8: return launch_probe_eta<4, 8>(a, g, sm, s, km);
-        case 16: return launch_probe_eta<4, 16>(a, g, sm, s, km);
-        case 32: return launch_probe_eta<4, 32>(a, g, sm, s, km);
+        case 1: return launch_probe_eta<4, 1>(a, g, sm, s, km, st);
+        case 2: return launch_probe_eta<4, 2>(a, g, sm, s, km, st);
+        case 4: return launch_probe_eta<4, 4>(a, g, sm, s, km, st);
+        case 8: return launch_probe_eta<4, 8>(a, g, sm, s, km, st);
+        case 16: return launch_probe_eta<4, 16>(a, g, sm, s, km, st);
+        case 32: return launch_probe_eta<4, 32>(a, g, sm, s, km, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -248,11 +307,12 @@ cudaError_t launch_probe(const ProbeArgs &a, const Geometry &g, int sm, cudaStre
 }  // namespace
 
 cudaError_t launch_probe_seqs(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s) {
-    return launch_probe(a, g, sm_count, s, false);
+    return launch_probe(a, g, sm_count, s, false, false);
 }
 
-cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s) {
-    return launch_probe(a, g, sm_count, s, true);
+cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_count, cudaStream_t s,
+                               bool staged) {
+    return launch_probe(a, g, sm_count, s, true, staged);
 }
 
 }  // namespace rgpu

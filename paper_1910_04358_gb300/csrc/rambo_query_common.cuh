@@ -16,6 +16,17 @@ __device__ __forceinline__ uint32_t reduce_pos(uint64_t h, uint64_t m, uint32_t 
     return (uint32_t)(m_pow2 ? (h & (m - 1)) : (h % m));
 }
 
+// 16-byte copy from global to shared memory that does not pass through
+// registers (caching in L2 only), and the wait for this thread's copies.
+__device__ __forceinline__ void cp_async16(uint4 *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Largest q in [0, n) with kcum[q] <= g, given kcum[0] <= g < kcum[n].
 __device__ __forceinline__ uint64_t find_query(const uint64_t *kcum, uint64_t n, uint64_t g) {
     uint64_t lo = 0, hi = n;

@@ -173,7 +173,8 @@ TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_p
                  "kmer_probe_ctas_per_sm", "host_chunk_kmers", "branch_priority",
                  "host_slots", "bin_region_kib", "bin_rows", "host_direct",
                  "expand_tc", "host_fused_ctas_per_sm",
-                 "insert_mode", "insert_bin_records", "fused_async")
+                 "insert_mode", "insert_bin_records", "fused_async",
+                 "kmer_async")
 
 
 class _Tuning(C.Structure):

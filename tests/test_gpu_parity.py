@@ -210,6 +210,12 @@ def test_fused_staged_gathers(rambo_lib, eta):
                dict(fused_async=0, fused_tile_kmers=64, fused_short_max=40)):
         idx.set_tuning(query_path=1, **st)
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want), st
+    # the single k-mer probe, staged the same way
+    kmers = synth.sample_kmers(rng, corpus, 3000, p.k, 0.5)
+    want_k = o.query_kmers(kmers)
+    for st in (dict(kmer_async=1), dict(kmer_async=1, kmer_probe_ctas_per_sm=1), dict(kmer_async=0)):
+        idx.set_tuning(**st)
+        assert np.array_equal(idx.query_kmers(kmers), want_k), st
 
 
 def test_tuning_knobs_do_not_change_results(rambo_lib):
@@ -352,7 +358,7 @@ def test_argument_errors(rambo_lib):
     # tuning knobs out of range are refused and leave the tuning unchanged
     before = idx.get_tuning()
     for bad in (dict(query_path=3), dict(host_slots=0), dict(host_slots=5), dict(bin_rows=3),
-                dict(insert_mode=4), dict(insert_bin_records=100), dict(fused_async=2), dict(expand_tc=2), dict(early_exit_segment=100)):
+                dict(insert_mode=4), dict(insert_bin_records=100), dict(fused_async=2), dict(kmer_async=2), dict(expand_tc=2), dict(early_exit_segment=100)):
         with pytest.raises(rambo_lib.RamboError):
             idx.set_tuning(**bad)
     assert idx.get_tuning() == before
