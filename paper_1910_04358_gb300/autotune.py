@@ -11,7 +11,8 @@ change launch shapes only).  Search: for every query path that this index
 geometry actually runs (a requested path the library cannot take for these
 groups falls back to another, and is then not a separate candidate), a
 coordinate descent over the other knobs, one knob at a time in the order of
-KNOBS, keeping the best value before moving on; the best of the paths wins.
+KNOBS, keeping the best value before moving on, repeated while a whole pass
+still improves (at most three passes); the best of the paths wins.
 Knobs of a path that does not run (the fused path's tile and short-query
 threshold, the binned path's regions) are not varied.
 """
@@ -77,13 +78,26 @@ def effective_path(tuning, info) -> int:
     return 0
 
 
-def _descend(idx, run, outputs, ref, start, knobs, reps, info, trials, verbose):
-    """Coordinate descent from `start` over `knobs`; returns (best, ms)."""
+def _descend(idx, run, outputs, ref, start, knobs, reps, info, trials, verbose, passes: int = 3):
+    """Coordinate descent from `start` over `knobs`, repeated while a whole
+    pass still improves (at most `passes`: a knob tuned early may want
+    another value once a later one has moved); returns (best, ms)."""
     import torch
     idx.set_tuning(**start)
     best_cfg, best_ms = dict(start), _time(run, reps)
     trials.append({"tuning": dict(start), "ms": best_ms})
     path = effective_path(start, info)
+    for _ in range(passes):
+        before = dict(best_cfg)
+        best_cfg, best_ms = _one_pass(idx, run, outputs, ref, best_cfg, best_ms, knobs, reps, path, trials,
+                                      verbose)
+        if best_cfg == before:
+            break
+    return best_cfg, best_ms
+
+
+def _one_pass(idx, run, outputs, ref, best_cfg, best_ms, knobs, reps, path, trials, verbose):
+    import torch
     for knob, values in knobs:
         if knob in ("fused_tile_kmers", "fused_short_max", "fused_async") and path != 1:
             continue

@@ -93,3 +93,25 @@ def test_autotune_rejects_a_candidate_that_changes_the_answers(monkeypatch):
     with pytest.raises(RuntimeError):
         autotune.autotune(idx, lambda: None, outputs, reps=1)
     assert idx.get_tuning() == start
+
+
+def test_autotune_revisits_a_knob_once_a_later_one_moves(monkeypatch):
+    # the expansion grid comes before the staged gathers in the search order;
+    # its best value flips once they are on, so one pass would stop short
+    import torch
+    from paper_1910_04358_gb300 import autotune
+    idx = _FakeIndex(16)
+
+    def cost(t):
+        if autotune.effective_path(t, idx.info) != 1:
+            return 2.0
+        e, a = t["expand_ctas_per_sm"], t["fused_async"]
+        if a == 0:
+            return 1.0 if e == 8 else 1.05
+        return {2: 0.90, 8: 0.98}.get(e, 1.0)
+
+    monkeypatch.setattr(autotune, "_time", lambda run, reps: cost(idx.t))
+    out = torch.zeros(4, dtype=torch.int32)
+    res = autotune.autotune(idx, lambda: None, lambda: [out], reps=1)
+    assert res["best"]["fused_async"] == 1 and res["best"]["expand_ctas_per_sm"] == 2
+    assert abs(res["ms"] - 0.90) < 1e-9
