@@ -375,7 +375,9 @@ typedef struct {
                                        /* (RAMBO_ENOMEM if it cannot be had)           */
     uint32_t insert_bin_records;       /* insert_mode 3: records the buffer holds      */
                                        /* (8 bytes each; 0 = 2^28, else >= 4096); a    */
-                                       /* batch is applied in chunks that fill it      */
+                                       /* batch is applied in chunks that fill it (a   */
+                                       /* batch needing over 65536 chunks is inserted  */
+                                       /* directly)                                    */
     uint32_t fused_async;              /* query_path 1, 16-byte groups, eta <= 2: 1 =  */
                                        /* the probes' gathers land in shared memory    */
                                        /* (cp.async) instead of registers, so the      */

@@ -539,26 +539,28 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     a.err = h->d_err;
     a.mode = h->tune.insert_mode;
     uint32_t rshift = 0;
-    const uint32_t nbins =
+    uint32_t nbins =
         a.mode == 3 && h->d_bins
             ? binned_insert_bins(g.m, g.Gw * 4, g.K,
                                  (uint64_t)(h->tune.bin_region_kib ? h->tune.bin_region_kib : 32768) * 1024,
                                  &rshift)
             : 0;
+    // chunks of the flat k-mer index sized to fill the record buffer (k-mers
+    // <= bases; chunks past the batch's k-mers do nothing); a buffer far too
+    // small for the batch takes the direct insert instead of a launch storm
+    const uint64_t per = h->bins_records / g.eta > 0 ? h->bins_records / g.eta : 1;
+    const uint64_t bound = packed_bytes * 4;
+    const uint64_t chunks = (bound + per - 1) / per;
+    if (chunks > IB_MAX_CHUNKS) nbins = 0;
     if (nbins) {
-        // chunks of the flat k-mer index sized to fill the record buffer
-        // (k-mers <= bases; chunks past the batch's k-mers do nothing)
         BinnedInsert b{h->d_bins, h->d_bin_count, h->bins_records / nbins, nbins, rshift};
-        const uint64_t per = h->bins_records / g.eta > 0 ? h->bins_records / g.eta : 1;
-        const uint64_t bound = packed_bytes * 4;
-        const uint64_t chunks = (bound + per - 1) / per;
         StageScope sc(h, RAMBO_STAGE_INSERT, s, (int)(2 * chunks));
         for (uint64_t f0 = 0; f0 < bound; f0 += per) {
             RAMBO_TRY(cudaMemsetAsync(h->d_bin_count, 0, (IB_MAX_BINS + 1) * 4, s));
             RAMBO_TRY(launch_insert_binned(a, b, f0, f0 + per, h->sm_count, s));
         }
     } else {
-        if (a.mode == 3) a.mode = 2;  // the index is too large for regions that fit in L2
+        if (a.mode == 3) a.mode = 2;  // too many regions, or too many chunks
         StageScope sc(h, RAMBO_STAGE_INSERT, s, 1);
         RAMBO_TRY(launch_insert(a, h->sm_count, s));
     }

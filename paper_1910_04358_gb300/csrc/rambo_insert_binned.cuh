@@ -11,6 +11,10 @@ namespace rgpu {
 // that stays in L2 while its records are applied).
 constexpr uint32_t IB_MAX_BINS = 1024;
 
+// Chunks one insert call may take (record buffer / eta k-mers each); a
+// batch needing more is inserted directly.
+constexpr uint64_t IB_MAX_CHUNKS = 65536;
+
 // A record is (position << IB_DOC_BITS) | document: positions below 2^40,
 // documents below 2^24.
 constexpr uint32_t IB_DOC_BITS = 24;
