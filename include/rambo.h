@@ -423,6 +423,24 @@ int rambo_probe_host_write(const void *src, void *dst_host, uint64_t bytes, uint
  * stays usable.  RAMBO_EINVAL for spins out of range. */
 int rambo_probe_wait_expiry(rambo_t *h, uint64_t spins, void *stream);
 
+/* L2 reduction rate on the current device: `blocks` CTAs of 256 threads,
+ * each thread ops_per_thread 64-bit atomicOr (no return value) at hashed
+ * word indices of `buf` (device, 8-byte aligned, `words` 8-byte words, a
+ * power of two).  With `buf` inside L2 this is the rate the region-binned
+ * insert's apply pass can reach.  Asynchronous on `stream`; the caller times
+ * it.  RAMBO_EINVAL for arguments out of range. */
+int rambo_probe_l2_atomics(void *buf, uint64_t words, uint32_t ops_per_thread, uint32_t blocks, void *stream);
+
+/* Tensor-memory read rate on the current device: one CTA per SM allocates all
+ * 512 tensor-memory columns; each of its `warps` (4, 8 or 16) warps issues
+ * `loads_in_flight` (1, 2 or 4) tcgen05.ld 32x32b.x32 before each wait,
+ * `iters` times, folding every register.  sink (device, SMs * warps * 32
+ * words) takes the folds; cycles (device, one per SM) the clock64 span of
+ * each CTA's loop.  Bytes read per CTA = warps * iters * loads_in_flight *
+ * 4096.  Asynchronous on `stream`.  RAMBO_EINVAL for arguments out of range. */
+int rambo_probe_tmem_read(uint32_t warps, uint32_t loads_in_flight, uint32_t iters, uint32_t *sink,
+                          long long *cycles, void *stream);
+
 /* Reads (into *previous) and, if bytes > 0, sets the current context's L2
  * fetch granularity limit (32, 64 or 128 bytes).  A per-process context
  * limit; it ends with the process. */

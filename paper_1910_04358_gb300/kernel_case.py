@@ -1,12 +1,14 @@
 """Small, self-contained launches of one query stage, for profiling.
 
-  python -m paper_1910_04358_gb300.kernel_case --case kmers|seqs
+  python -m paper_1910_04358_gb300.kernel_case --case kmers|seqs|build
          [--workload medium|large|stream] [--reps N] [--query-path 0|1]
 
 Builds the workload's index on cuda:0, then runs the chosen query batch
 `reps` times (kmers: the medium workload's 10^6 single 31-mers; seqs: its
 sequence batch) so a profiler can capture single launches of the probe,
-expansion or fused kernels on a realistic index.  The stream workload
+expansion or fused kernels on a realistic index.  `build` builds the index
+`reps` times into fresh handles (the tuning's insert mode) and prints each
+build's insert-stage time from the library's CUDA events.  The stream workload
 inserts its first `--epochs` epochs of documents (its full document
 geometry: 10^5 document bits per answer, R = 6, B = 316) and queries the
 last epoch's batch.
@@ -21,7 +23,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["kmers", "seqs"], default="kmers")
+    ap.add_argument("--case", choices=["kmers", "seqs", "build"], default="kmers")
     ap.add_argument("--workload", choices=["medium", "large", "stream"], default="medium")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--query-path", type=int, default=0)
@@ -50,6 +52,8 @@ def main(argv=None):
     if a.m:
         p = synth.Params(K=p.K, B=p.B, R=p.R, m=a.m, eta=p.eta, k=p.k, seed=p.seed)
     dev = lambda x, dt: torch.from_numpy(np.ascontiguousarray(x).view(dt)).cuda()
+    if a.case == "build":
+        return build_case(a, corpus, p, dev)
     idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=0)
     if a.tuning_from_cache:
         from . import autotune
@@ -77,6 +81,24 @@ def main(argv=None):
             idx.query_seqs_dev(dp, do, out=out)
     idx.sync()
     print("ok", a.case, a.workload, int(out.sum().item()))
+    return 0
+
+
+def build_case(a, corpus, p, dev):
+    from . import rambo
+    d_ids, d_p, d_o = dev(corpus.doc_ids, np.int32), dev(corpus.packed, np.uint8), dev(corpus.offsets, np.int64)
+    kmers = int(np.maximum(np.diff(corpus.offsets.astype(np.int64)) - p.k + 1, 0).sum())
+    for _ in range(a.reps):
+        idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=0)
+        if a.tune:
+            idx.set_tuning(**{kv.split("=")[0]: int(kv.split("=")[1]) for kv in a.tune})
+        idx.profile_reset(timed_stages=("insert",))
+        idx.insert_batch_dev(d_ids, d_p, d_o)
+        idx.sync()
+        ms = idx.profile_read()["insert"]["ms"]
+        print(f"build {a.workload} insert_mode {idx.get_tuning()['insert_mode']}: {ms:.2f} ms, "
+              f"{kmers / (ms / 1e3):.3e} k-mers/s", flush=True)
+        idx.close()
     return 0
 
 

@@ -87,6 +87,8 @@ def load():
             "rambo_query_words_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
             "rambo_query_batch": (i, [p, u64, p, p, u64, p, p, p]),
             "rambo_probe_host_write": (i, [p, p, u64, u32, p]),
+            "rambo_probe_l2_atomics": (i, [p, u64, u32, u32, p]),
+            "rambo_probe_tmem_read": (i, [u32, u32, u32, p, p, p]),
             "rambo_probe_wait_expiry": (i, [p, u64, p]),
             "rambo_query_batch_workspace": (sz, [p, u64, u64, u64]),
             "rambo_query_seqs_workspace_for": (sz, [p, u64, u64]),
@@ -191,6 +193,20 @@ def probe_gather(buf, record_bytes: int, n_probes: int, variant: int = 0, seed: 
                                      unroll, seed, sink.data_ptr(), _stream_handle(stream)),
            "rambo_probe_gather")
     return sink
+
+
+def probe_l2_atomics(buf, ops_per_thread: int, blocks: int, stream=None):
+    """64-bit atomicOr at hashed words of `buf` (a CUDA tensor of 8-byte
+    words, a power of two of them); the caller times it on `stream`."""
+    _check(load().rambo_probe_l2_atomics(buf.data_ptr(), buf.numel(), ops_per_thread, blocks,
+                                         _stream_handle(stream)), "rambo_probe_l2_atomics")
+
+
+def probe_tmem_read(warps: int, loads_in_flight: int, iters: int, sink, cycles, stream=None):
+    """Tensor-memory reads, one CTA per SM (see rambo.h); `sink` a CUDA int32
+    tensor of SMs * warps * 32 words, `cycles` a CUDA int64 tensor of SMs."""
+    _check(load().rambo_probe_tmem_read(warps, loads_in_flight, iters, sink.data_ptr(), cycles.data_ptr(),
+                                        _stream_handle(stream)), "rambo_probe_tmem_read")
 
 
 def probe_host_write(src, dst_pinned, blocks_per_sm: int = 4, stream=None):

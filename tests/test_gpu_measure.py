@@ -53,3 +53,14 @@ def test_bounded_wait_expiry_is_reported_and_handle_stays_usable(rambo_lib):
     assert np.array_equal(idx.query_seqs(q.packed, q.offsets), o.query_seqs(q.packed, q.offsets))
     with pytest.raises(rambo_lib.RamboError):
         idx.probe_wait_expiry(0)
+
+
+@pytest.mark.gpu
+def test_hardware_rate_probes_run():
+    # the two probes behind design notes: L2 atomics in and out of L2, and
+    # tensor-memory reads; small runs, checked only for sane output
+    from paper_1910_04358_gb300 import hw_probe
+    rows = list(hw_probe.l2_atomics([8, 256], ops=16, reps=1))
+    assert len(rows) == 2 and all(r["g_atomicor_per_s"] > 0 for r in rows)
+    rows = list(hw_probe.tmem_read(iters=64))
+    assert len(rows) == 9 and all(r["bytes_per_cycle_per_sm"] > 0 for r in rows)
