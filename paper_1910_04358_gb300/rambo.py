@@ -9,7 +9,6 @@ module raises.
 from __future__ import annotations
 
 import ctypes as C
-import os
 import threading
 
 import numpy as np
