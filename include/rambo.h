@@ -350,11 +350,6 @@ typedef struct {
                                        /* page-locked and device-addressable (each     */
                                        /* must be one such allocation); others are     */
                                        /* staged and copied as with 0 (the default)    */
-    uint32_t expand_tc;                /* 1: expansion on the tensor cores (an exact   */
-                                       /* 0/1 product of bucket masks and the          */
-                                       /* transposed bucket->document bitmaps) when    */
-                                       /* R*B + 2 <= 256, R <= 15 and the bitmaps fit  */
-                                       /* in shared memory                             */
     uint32_t host_fused_ctas_per_sm;   /* host-buffer batches with both kinds: the     */
                                        /* persistent fused launch takes at most this   */
                                        /* many CTAs per SM (0 = as probe_ctas_per_sm;  */
@@ -405,46 +400,13 @@ int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t record_byte
                        uint64_t n_probes, uint32_t load_variant, uint32_t unroll, uint64_t seed,
                        void *sink, void *stream);
 
-/* Copies `bytes` (a multiple of 16) from device memory `src` into page-locked
- * host memory `dst_host` with 16-byte stores issued by SMs_count x
- * blocks_per_sm blocks (SM-driven copy-out over the host link, to compare
- * with the copy engine).  RAMBO_EINVAL if dst_host is not device-addressable
- * page-locked host memory (cudaHostAlloc, cudaMallocHost, registered) or an
- * argument is out of range.  Asynchronous on `stream`. */
-int rambo_probe_host_write(const void *src, void *dst_host, uint64_t bytes, uint32_t blocks_per_sm,
-                           void *stream);
-
 /* Failure-detection check: enqueues on `stream` one kernel whose thread
- * waits on an mbarrier that nothing ever completes, with the bounded polling
- * wait that the tensor-core expansion's warps use to hand work to each other,
- * here of `spins` polls (1..2^22) instead of the kernel's 2^26.  The
- * wait runs out and latches the error that the next rambo_sync on that
- * stream reports as RAMBO_ETIMEOUT; nothing faults or hangs, and the handle
- * stays usable.  RAMBO_EINVAL for spins out of range. */
+ * polls, without suspending, an mbarrier that nothing ever completes, and
+ * gives up after `spins` polls (1..2^22).  The wait runs out and latches the
+ * error that the next rambo_sync on that stream reports as RAMBO_ETIMEOUT;
+ * nothing faults or hangs, and the handle stays usable.  RAMBO_EINVAL for
+ * spins out of range. */
 int rambo_probe_wait_expiry(rambo_t *h, uint64_t spins, void *stream);
-
-/* L2 reduction rate on the current device: `blocks` CTAs of 256 threads,
- * each thread ops_per_thread 64-bit atomicOr (no return value) at hashed
- * word indices of `buf` (device, 8-byte aligned, `words` 8-byte words, a
- * power of two).  With `buf` inside L2 this is the rate the region-binned
- * insert's apply pass can reach.  Asynchronous on `stream`; the caller times
- * it.  RAMBO_EINVAL for arguments out of range. */
-int rambo_probe_l2_atomics(void *buf, uint64_t words, uint32_t ops_per_thread, uint32_t blocks, void *stream);
-
-/* Tensor-memory read rate on the current device: one CTA per SM allocates all
- * 512 tensor-memory columns; each of its `warps` (4, 8 or 16) warps issues
- * `loads_in_flight` (1, 2 or 4) tcgen05.ld 32x32b.x32 before each wait,
- * `iters` times, folding every register.  sink (device, SMs * warps * 32
- * words) takes the folds; cycles (device, one per SM) the clock64 span of
- * each CTA's loop.  Bytes read per CTA = warps * iters * loads_in_flight *
- * 4096.  Asynchronous on `stream`.  RAMBO_EINVAL for arguments out of range. */
-int rambo_probe_tmem_read(uint32_t warps, uint32_t loads_in_flight, uint32_t iters, uint32_t *sink,
-                          long long *cycles, void *stream);
-
-/* Reads (into *previous) and, if bytes > 0, sets the current context's L2
- * fetch granularity limit (32, 64 or 128 bytes).  A per-process context
- * limit; it ends with the process. */
-int rambo_set_l2_fetch_granularity(int bytes, int *previous);
 
 /* ---------------------------------------------------------------------- */
 /* Profiling.  The library counts every kernel it launches, per stage, and */

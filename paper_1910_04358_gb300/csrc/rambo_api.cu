@@ -374,8 +374,6 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
             ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                          h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
                          h->tune.expand_filter};
-            e.tc = h->tune.expand_tc;
-            e.err = h->d_err;
             StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
             RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
             return RAMBO_OK;
@@ -401,8 +399,6 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                      h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
                      h->tune.expand_filter};
-        e.tc = h->tune.expand_tc;
-        e.err = h->d_err;
         FusedQueues qs{};
         qs.counters = reinterpret_cast<uint32_t *>(w + L.qcnt);
         qs.short_list = reinterpret_cast<uint32_t *>(w + L.slist);
@@ -457,8 +453,6 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                      h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
                      h->tune.expand_filter};
-    e.tc = h->tune.expand_tc;
-    e.err = h->d_err;
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
         RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
@@ -491,8 +485,6 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
     ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                      h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
                      h->tune.expand_filter};
-    e.tc = h->tune.expand_tc;
-    e.err = h->d_err;
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
         RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
@@ -866,7 +858,6 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.bin_region_kib = 32768;
     h->tune.bin_rows = 2;
     h->tune.host_direct = 0;
-    h->tune.expand_tc = 0;
     h->tune.host_fused_ctas_per_sm = 1;
     h->tune.insert_mode = 2;
     h->tune.insert_bin_records = 0;
@@ -1198,8 +1189,6 @@ int rambo_query_words_dev(rambo_t *h, uint64_t n, const uint8_t *bytes, uint64_t
     }
     ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                  h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K, h->tune.expand_filter};
-    e.tc = h->tune.expand_tc;
-    e.err = h->d_err;
     {
         StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
         RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
@@ -1345,7 +1334,7 @@ int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
         t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2 ||
         t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22) ||
         (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
-        t->host_direct > 1 || t->expand_tc > 1 || t->host_fused_ctas_per_sm > 32 ||
+        t->host_direct > 1 || t->host_fused_ctas_per_sm > 32 ||
         t->insert_mode > 3 || (t->insert_bin_records != 0 && t->insert_bin_records < 4096) ||
         t->fused_async > 1 || t->kmer_async > 1)
         return RAMBO_EINVAL;

@@ -94,34 +94,8 @@ cudaError_t launch_gather_u(const void *buf, uint64_t n_records, uint64_t n_prob
     return launch_gather_v<LPR, 4>(buf, n_records, n_probes, variant, seed, sink, blocks, s);
 }
 
-// Streams src (device) into dst (device address of mapped page-locked host
-// memory) with 16-byte loads and stores: SM-driven copy-out over the
-// host link, to compare with the copy engine.
-__global__ void __launch_bounds__(GATHER_THREADS) k_host_write(const uint4 *src, uint4 *dst, uint64_t n16) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        dst[i] = __ldg(src + i);
-}
-
 }  // namespace
 }  // namespace rgpu
-
-extern "C" int rambo_probe_host_write(const void *src, void *dst_host, uint64_t bytes, uint32_t blocks_per_sm,
-                                      void *stream) {
-    using namespace rgpu;
-    if (!src || !dst_host || !bytes || (bytes & 15) || (reinterpret_cast<uintptr_t>(src) & 15) ||
-        (reinterpret_cast<uintptr_t>(dst_host) & 15) || blocks_per_sm == 0 || blocks_per_sm > 32)
-        return RAMBO_EINVAL;
-    void *dst = mapped_host_range(dst_host, bytes);
-    if (!dst) return RAMBO_EINVAL;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return RAMBO_ECUDA;
-    k_host_write<<<sms * (int)blocks_per_sm, GATHER_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const uint4 *>(src), static_cast<uint4 *>(dst), bytes / 16);
-    return cudaGetLastError() == cudaSuccess ? RAMBO_OK : RAMBO_ECUDA;
-}
 
 extern "C" int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t record_bytes,
                                   uint64_t n_probes, uint32_t load_variant, uint32_t unroll,
@@ -150,14 +124,4 @@ extern "C" int rambo_probe_gather(const void *buf, uint64_t buf_bytes, uint32_t 
         default: e = launch_gather_u<32>(buf, n_records, n_probes, load_variant, unroll, seed, sk, blocks, s); break;
     }
     return e == cudaSuccess ? RAMBO_OK : RAMBO_ECUDA;
-}
-
-extern "C" int rambo_set_l2_fetch_granularity(int bytes, int *previous) {
-    size_t prev = 0;
-    if (cudaDeviceGetLimit(&prev, cudaLimitMaxL2FetchGranularity) != cudaSuccess) return RAMBO_ECUDA;
-    if (previous) *previous = (int)prev;
-    if (bytes <= 0) return RAMBO_OK;
-    if (bytes != 32 && bytes != 64 && bytes != 128) return RAMBO_EINVAL;
-    return cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) == cudaSuccess ? RAMBO_OK
-                                                                                            : RAMBO_ECUDA;
 }

@@ -15,7 +15,7 @@ enum : uint32_t {
     ERR_KMER_CODE = 2u,     // k-mer code with a bit at or above 2k
     ERR_OFFSETS = 4u,       // decreasing offsets or offsets past the buffer
     ERR_QUEUE = 8u,         // a work-queue claim loop exceeded its bound
-    ERR_WAIT = 16u,         // a tensor-core completion wait exceeded its bound
+    ERR_WAIT = 16u,         // a bounded device wait ran out
 };
 
 // ---------------------------------------------------------------------------
@@ -200,8 +200,6 @@ struct ExpandArgs {
     const uint32_t *phi;     // K x R partition (candidate filtering)
     uint32_t K;
     uint32_t filter;         // 1: expand by candidate filtering when it fits
-    uint32_t tc;             // 1: expand on the tensor cores when it fits
-    uint32_t *err;           // latched device errors (tensor-core waits)
 };
 
 struct InsertArgs {
@@ -316,11 +314,6 @@ cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry
 
 // max_blocks caps the expansion grid
 cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cudaStream_t s);
-// Tensor-core expansion (R*B + 2 <= 256, R <= 15, the transposed bitmaps
-// fit in shared memory): the shared memory it needs, 0 if it does not apply;
-// the launcher needs a.err.
-size_t expand_tc_smem(const ExpandArgs &a);
-cudaError_t launch_expand_tc(const ExpandArgs &a, int sm_count, cudaStream_t s);
 // A bounded mbarrier wait that nothing completes; latches ERR_WAIT on expiry.
 cudaError_t launch_wait_expiry(uint32_t *err, uint64_t spins, cudaStream_t s);
 uint64_t bytetab_words(uint32_t B, uint32_t R, uint32_t W);

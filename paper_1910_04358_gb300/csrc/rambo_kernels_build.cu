@@ -426,4 +426,37 @@ cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Failure-detection check of a bounded device wait: one thread polls an
+// mbarrier that nothing ever completes (no arrivals are made), without
+// suspending, and gives up after `spins` polls by latching ERR_WAIT.  Nothing
+// faults or hangs; the host reads the latched word as RAMBO_ETIMEOUT.
+namespace {
+__global__ void k_wait_expiry(uint32_t *err, uint64_t spins) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1u) : "memory");
+    for (uint64_t i = 0;; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(b), "r"(0u)
+            : "memory");
+        if (ok) return;
+        if (i >= spins) {
+            atomicOr(err, ERR_WAIT);
+            return;
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_wait_expiry(uint32_t *err, uint64_t spins, cudaStream_t s) {
+    k_wait_expiry<<<1, 32, 0, s>>>(err, spins);
+    return cudaGetLastError();
+}
+
 }  // namespace rgpu

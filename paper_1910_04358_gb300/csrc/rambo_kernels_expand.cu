@@ -315,7 +315,6 @@ int nib_grid(int occ, int sm_count, int max_blocks, uint64_t n) {
 
 cudaError_t launch_expand(const ExpandArgs &a, int max_blocks, int sm_count, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    if (a.tc && a.err && expand_tc_smem(a)) return launch_expand_tc(a, sm_count, s);
     const uint32_t wc = (a.W + 31) / 32;
     const int C = wc >= 8 ? 8 : wc >= 4 ? 4 : wc >= 2 ? 2 : 1;
     const uint64_t units = a.n * ((a.W + 32 * C - 1) / (32 * C));

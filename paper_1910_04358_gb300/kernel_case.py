@@ -1,7 +1,7 @@
 """Small, self-contained launches of one query stage, for profiling.
 
-  python -m paper_1910_04358_gb300.kernel_case --case kmers|seqs|build
-         [--workload medium|large|stream] [--reps N] [--query-path 0|1]
+  python -m paper_1910_04358_gb300.kernel_case --case kmers|seqs|build|gather
+         [--workload medium|large|stream] [--reps N] [--query-path 0|1|2]
 
 Builds the workload's index on cuda:0, then runs the chosen query batch
 `reps` times (kmers: the medium workload's 10^6 single 31-mers; seqs: its
@@ -12,6 +12,12 @@ build's insert-stage time from the library's CUDA events.  The stream workload
 inserts its first `--epochs` epochs of documents (its full document
 geometry: 10^5 document bits per answer, R = 6, B = 316) and queries the
 last epoch's batch.
+
+`gather` times the random-record gather (rambo_probe_gather: random records of
+16..512 bytes from a device buffer, no hashing or bit logic) over record
+sizes, loads in flight per lane and buffer sizes, one JSON object per point:
+a probe of the index reads one group of G bytes at a random position, so the
+row for record = max(G, 16) bounds what the probe kernels can reach.
 """
 from __future__ import annotations
 
@@ -23,7 +29,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["kmers", "seqs", "build"], default="kmers")
+    ap.add_argument("--case", choices=["kmers", "seqs", "build", "gather"], default="kmers")
     ap.add_argument("--workload", choices=["medium", "large", "stream"], default="medium")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--query-path", type=int, default=0)
@@ -34,7 +40,14 @@ def main(argv=None):
     ap.add_argument("--m", type=int, default=None, help="bits per filter (smaller index)")
     ap.add_argument("--n-queries", type=int, default=None, help="fewer sequence queries (large)")
     ap.add_argument("--epochs", type=int, default=3, help="insert epochs before the query (stream)")
+    ap.add_argument("--buf-gb", type=float, nargs="+", default=[1.0, 64.0], help="gather: buffer sizes")
+    ap.add_argument("--records", type=int, nargs="+", default=[16, 32, 64, 128, 256, 512],
+                    help="gather: record bytes")
+    ap.add_argument("--unroll", type=int, nargs="+", default=[4, 8, 16, 32],
+                    help="gather: 16-byte loads in flight per lane")
     a = ap.parse_args(argv)
+    if a.case == "gather":
+        return gather_case(a)
     import torch
 
     from . import rambo, synth
@@ -132,6 +145,38 @@ def stream_case(a):
         idx.query_seqs_dev(dp, do, out=out)
     idx.sync()
     print("ok", a.case, a.workload, int(out.sum().item()))
+    return 0
+
+
+def gather_case(a, useful_gb=2.0):
+    import json
+
+    import torch
+
+    from . import rambo
+    rambo.load()
+    for size_gb in a.buf_gb:
+        buf = torch.empty(int(size_gb * (1 << 30)), dtype=torch.uint8, device="cuda")
+        buf.fill_(3)
+        sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+        for rb in a.records:
+            n = int(useful_gb * (1 << 30)) // rb
+            for u in a.unroll:
+                rambo.probe_gather(buf, rb, n, 0, 7, sink, unroll=u)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                best = float("inf")
+                for r in range(max(1, a.reps)):
+                    e0.record()
+                    rambo.probe_gather(buf, rb, n, 0, 11 + r, sink, unroll=u)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                print(json.dumps({"buf_gb": size_gb, "record_bytes": rb, "unroll": u, "ms": best,
+                                  "probes_per_s": n / best * 1e3, "useful_gb_s": n * rb / best / 1e6,
+                                  "line_gb_s": n * max(rb, 128) / best / 1e6}), flush=True)
+        del buf
+        torch.cuda.empty_cache()
     return 0
 
 

@@ -75,7 +75,6 @@ def load():
             "rambo_get_tuning": (i, [p, C.c_void_p]),
             "rambo_set_tuning": (i, [p, C.c_void_p]),
             "rambo_probe_gather": (i, [p, u64, u32, u64, u32, u32, u64, p, p]),
-            "rambo_set_l2_fetch_granularity": (i, [i, C.POINTER(i)]),
             "rambo_query_seqs_noalloc": (i, [p, u64, p, u64, p, p, p]),
             "rambo_query_ranges_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
             "rambo_fold": (i, [p]),
@@ -85,9 +84,6 @@ def load():
             "rambo_query_words_workspace": (sz, [p, u64]),
             "rambo_query_words_dev": (i, [p, u64, p, u64, p, p, p, p, sz, p]),
             "rambo_query_batch": (i, [p, u64, p, p, u64, p, p, p]),
-            "rambo_probe_host_write": (i, [p, p, u64, u32, p]),
-            "rambo_probe_l2_atomics": (i, [p, u64, u32, u32, p]),
-            "rambo_probe_tmem_read": (i, [u32, u32, u32, p, p, p]),
             "rambo_probe_wait_expiry": (i, [p, u64, p]),
             "rambo_query_batch_workspace": (sz, [p, u64, u64, u64]),
             "rambo_query_seqs_workspace_for": (sz, [p, u64, u64]),
@@ -173,7 +169,7 @@ TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_p
                  "expand_filter", "early_exit", "early_exit_segment",
                  "kmer_probe_ctas_per_sm", "host_chunk_kmers", "branch_priority",
                  "host_slots", "bin_region_kib", "bin_rows", "host_direct",
-                 "expand_tc", "host_fused_ctas_per_sm",
+                 "host_fused_ctas_per_sm",
                  "insert_mode", "insert_bin_records", "fused_async",
                  "kmer_async")
 
@@ -192,35 +188,6 @@ def probe_gather(buf, record_bytes: int, n_probes: int, variant: int = 0, seed: 
                                      unroll, seed, sink.data_ptr(), _stream_handle(stream)),
            "rambo_probe_gather")
     return sink
-
-
-def probe_l2_atomics(buf, ops_per_thread: int, blocks: int, stream=None):
-    """64-bit atomicOr at hashed words of `buf` (a CUDA tensor of 8-byte
-    words, a power of two of them); the caller times it on `stream`."""
-    _check(load().rambo_probe_l2_atomics(buf.data_ptr(), buf.numel(), ops_per_thread, blocks,
-                                         _stream_handle(stream)), "rambo_probe_l2_atomics")
-
-
-def probe_tmem_read(warps: int, loads_in_flight: int, iters: int, sink, cycles, stream=None):
-    """Tensor-memory reads, one CTA per SM (see rambo.h); `sink` a CUDA int32
-    tensor of SMs * warps * 32 words, `cycles` a CUDA int64 tensor of SMs."""
-    _check(load().rambo_probe_tmem_read(warps, loads_in_flight, iters, sink.data_ptr(), cycles.data_ptr(),
-                                        _stream_handle(stream)), "rambo_probe_tmem_read")
-
-
-def probe_host_write(src, dst_pinned, blocks_per_sm: int = 4, stream=None):
-    """SM-driven copy of a CUDA tensor into a page-locked CPU tensor (measurement support)."""
-    _check(load().rambo_probe_host_write(src.data_ptr(), dst_pinned.data_ptr(),
-                                         src.numel() * src.element_size(), blocks_per_sm,
-                                         _stream_handle(stream)), "rambo_probe_host_write")
-
-
-def set_l2_fetch_granularity(nbytes: int) -> int:
-    """Sets this process's L2 fetch granularity limit; returns the previous value."""
-    prev = C.c_int(0)
-    _check(load().rambo_set_l2_fetch_granularity(nbytes, C.byref(prev)),
-           "rambo_set_l2_fetch_granularity")
-    return prev.value
 
 
 class _Profile(C.Structure):

@@ -242,9 +242,7 @@ def test_tuning_knobs_do_not_change_results(rambo_lib):
                 dict(query_path=0, use_nibble_table=1, expand_ctas_per_sm=1),
                 dict(query_path=0, use_nibble_table=0),
                 dict(query_path=2, bin_region_kib=0),
-                dict(query_path=2, bin_region_kib=4),
-                dict(query_path=0, expand_tc=1),
-                dict(query_path=2, expand_tc=1)]
+                dict(query_path=2, bin_region_kib=4)]
     for st in settings:
         idx.set_tuning(**st)
         assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want_s), st
@@ -358,7 +356,8 @@ def test_argument_errors(rambo_lib):
     # tuning knobs out of range are refused and leave the tuning unchanged
     before = idx.get_tuning()
     for bad in (dict(query_path=3), dict(host_slots=0), dict(host_slots=5), dict(bin_rows=3),
-                dict(insert_mode=4), dict(insert_bin_records=100), dict(fused_async=2), dict(kmer_async=2), dict(expand_tc=2), dict(early_exit_segment=100)):
+                dict(insert_mode=4), dict(insert_bin_records=100), dict(fused_async=2), dict(kmer_async=2),
+                dict(early_exit_segment=100)):
         with pytest.raises(rambo_lib.RamboError):
             idx.set_tuning(**bad)
     assert idx.get_tuning() == before
@@ -404,8 +403,7 @@ def test_expansion_variants_on_many_kmer_queries(rambo_lib, K, B, R):
     o = oracle_index(p, corpus)
     want = o.query_kmers(kmers, threads=4)
     idx = gpu_index(rambo_lib, p, corpus)
-    for st in (dict(expand_tc=1),
-               dict(expand_tc=0, expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=1),
+    for st in (dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=1),
                dict(expand_ctas_per_sm=1, use_nibble_table=1, expand_filter=0),
                dict(expand_ctas_per_sm=8, use_nibble_table=1, expand_filter=0),
                dict(expand_ctas_per_sm=1, use_nibble_table=0, smem_docbits=1),
@@ -415,11 +413,6 @@ def test_expansion_variants_on_many_kmer_queries(rambo_lib, K, B, R):
         got = idx.query_kmers_dev(_dev(kmers, np.int64))
         idx.sync()
         assert np.array_equal(rambo_lib.as_u32(got), want), st
-    # the tensor-core expansion on a batch smaller than one 128-query tile
-    idx.set_tuning(expand_tc=1)
-    got = idx.query_kmers_dev(_dev(kmers[:5], np.int64))
-    idx.sync()
-    assert np.array_equal(rambo_lib.as_u32(got), want[:5])
 
 
 def test_sequence_batch_past_single_block_scan(rambo_lib):
