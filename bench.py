@@ -2,14 +2,16 @@
 """Benchmark of the batched RAMBO query on one GB300.
 
 One step = one pass of the whole query path (k-mer extraction, hashing,
-probing, bucket-space AND, expansion to document masks) over one batch:
-the medium workload's 10^6 single 31-mers plus 10^4 sequences of 1 kbp,
-against an index of 1,000 documents x 1 Mbp (R=4, B=32, m=2^26, eta=2).
-The index is built once before timing (build throughput is reported beside
-the query numbers).  Prints one JSON line.
+probing, bucket-space AND, expansion to document masks) over one batch.  The
+default workload is the large index: 10,000 documents x 500 kbp (200 seed
+genomes, 0.5% substitutions, 0.05% indels), R=5, B=100, m=2^29, eta=2 (a
+32 GiB index), and a batch of 10^5 sequences of U[31, 5000] bp, 70% drawn
+from documents with 0.1% read errors.  The index is built once before timing
+(build throughput is reported beside the query numbers); a sample of the
+timed answers is checked against the CPU oracle.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload medium|large|tiny]
+                  [--workload large|medium|tiny|stream]
 
 --impl reference times the CPU oracle (plain single-pass RAMBO in C) on the
 host cores, on a bounded sample of the same workload per step.
@@ -276,7 +278,7 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 # serving (continuous batching vs plain fixed batches, same trace)
 
 
-def serving_section(idx, corpus, n_req: int, fracs=(0.25, 0.5, 0.75, 0.9), seed: int = 4):
+def serving_section(idx, corpus, n_req: int, fracs=(0.1, 0.25, 0.5, 0.75, 0.9, 1.1), seed: int = 4):
     from paper_1910_04358_gb300 import serve, synth
     rng = np.random.default_rng([synth.GEN_SEED_BASE + 4, seed])
     _, lengths = synth.serving_trace(rng, n_req, rate_per_s=1.0)
@@ -306,35 +308,80 @@ def serving_section(idx, corpus, n_req: int, fracs=(0.25, 0.5, 0.75, 0.9), seed:
 # CPU oracle legs
 
 
-def oracle_sample(p, corpus, kmers, q, frac_kmers: int, frac_seqs: int, threads: int):
-    """Restricted-mode oracle for a sample of the batch: tracks only the probe
-    positions the sample touches (exact for those queries)."""
-    import oracle
-    ks = kmers[::frac_kmers] if kmers.size else kmers
-    sel = np.arange(0, q.n, frac_seqs)
-    offs = q.offsets.astype(np.int64)
-    seq_offs = np.concatenate([[0], np.cumsum(offs[sel + 1] - offs[sel])]).astype(np.uint64)
-    # gather the sampled sequences into one packed stream
-    from paper_1910_04358_gb300 import synth
-    stream = synth.PackedStream()
-    for i in sel:
-        stream.append(synth.unpack_bases(q.packed, int(offs[i]), int(offs[i + 1] - offs[i])))
-    s_packed, s_offs = stream.finish()
-    probe = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, tracked=[0])
-    pos = set()
-    for x in ks.tolist():
-        c = oracle.canonical_of_code(int(x), p.k)
-        pos.update(probe.probe_position(c, j) for j in range(p.eta))
-    for i in range(s_offs.size - 1):
-        for t in range(int(s_offs[i]), int(s_offs[i + 1]) - p.k + 1):
-            c = oracle.kmer_canonical(s_packed, t, p.k)
-            pos.update(probe.probe_position(c, j) for j in range(p.eta))
-    probe.close()
-    o = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, tracked=sorted(pos))
-    t0 = time.time()
-    o.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets, threads=threads)
-    build_s = time.time() - t0
-    return o, ks, s_packed, s_offs, build_s
+def sample_fracs(workload: str):
+    """Every fk-th single k-mer and every fs-th sequence of the batch form
+    the oracle's sample (sequences of every length bucket)."""
+    return (200, 100) if workload == "medium" else (1, 50)
+
+
+class OracleSample:
+    """Restricted-mode oracle for a sample of the batch: it tracks only the
+    probe positions the sample touches, which is exact for those queries."""
+
+    def __init__(self, p, kmers, q, frac_kmers: int, frac_seqs: int):
+        import oracle
+        from paper_1910_04358_gb300 import synth
+        self.p = p
+        self.ks = kmers[::frac_kmers] if kmers.size else kmers
+        self.k_sel = np.arange(0, kmers.size, frac_kmers)
+        self.sel = np.arange(0, q.n, frac_seqs)
+        offs = q.offsets.astype(np.int64)
+        stream = synth.PackedStream()
+        for i in self.sel:
+            stream.append(synth.unpack_bases(q.packed, int(offs[i]), int(offs[i + 1] - offs[i])))
+        self.s_packed, self.s_offs = stream.finish()
+        self.o = oracle.tracking_oracle(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed,
+                                        seqs=[(self.s_packed, self.s_offs)], kmers=self.ks)
+        self.build_s = None
+        self.want_k = self.want_s = None
+        self.error = None
+        self._thread = None
+
+    def build(self, corpus, threads: int):
+        t0 = time.time()
+        self.o.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets, threads=threads)
+        self.build_s = time.time() - t0
+
+    def answer(self, threads: int):
+        self.want_k = self.o.query_kmers(self.ks, threads=threads) if self.ks.size else None
+        self.want_s = self.o.query_seqs(self.s_packed, self.s_offs, threads=threads)
+
+    def start(self, corpus, threads: int):
+        """Builds and answers on a host thread (the C oracle releases the
+        interpreter lock), so the GPU sections run meanwhile."""
+        def run():
+            try:
+                self.build(corpus, threads)
+                self.answer(threads)
+            except Exception as ex:  # reported by check()
+                self.error = repr(ex)
+        self._thread = threading.Thread(target=run, daemon=True)
+        self._thread.start()
+
+    def join(self):
+        if self._thread is not None:
+            self._thread.join()
+            self._thread = None
+
+    def check(self, out_k, out_s) -> dict:
+        """Compares the sampled rows of the GPU outputs with the oracle."""
+        from paper_1910_04358_gb300 import rambo
+        self.join()
+        if self.error:
+            return {"ok": False, "error": self.error}
+        got_s = rambo.as_u32(out_s)[self.sel]
+        bad_s = int(np.sum(np.any(got_s != self.want_s, axis=1)))
+        bad_k = 0
+        if self.want_k is not None and out_k is not None:
+            got_k = rambo.as_u32(out_k)[self.k_sel]
+            bad_k = int(np.sum(np.any(got_k != self.want_k, axis=1)))
+        L = np.diff(self.s_offs.astype(np.int64))
+        return {"ok": bad_s == 0 and bad_k == 0, "sequences_checked": int(self.sel.size),
+                "kmers_checked": int(self.ks.size), "mismatched_sequences": bad_s,
+                "mismatched_kmers": bad_k,
+                "sequence_lengths": [int(L.min()), int(L.max())] if L.size else None,
+                "oracle_build_s": self.build_s,
+                "what": "the timed step's answers, sampled rows, vs the restricted-mode CPU oracle"}
 
 
 def time_oracle(o, ks, s_packed, s_offs, threads: int):
@@ -358,14 +405,16 @@ def run_reference(args):
     corpus, kmers, q, desc = load_workload(args.workload)
     p = corpus.params
     threads = os.cpu_count() or 1
-    fk, fs = (200, 100) if args.workload == "medium" else (1, 50)
+    fk, fs = sample_fracs(args.workload)
     log(f"[reference] building restricted-mode oracle index on {threads} threads")
-    o, ks, sp, so, build_s = oracle_sample(p, corpus, kmers, q, fk, fs, threads)
+    osm = OracleSample(p, kmers, q, fk, fs)
+    osm.build(corpus, threads)
+    ks, sp, so = osm.ks, osm.s_packed, osm.s_offs
     units = sample_kmers_count(p, ks, so)
     bp = int(ks.size) * p.k + int(so[-1])
     for _ in range(args.warmup):
-        time_oracle(o, ks, sp, so, threads)
-    times = [time_oracle(o, ks, sp, so, threads) for _ in range(args.steps)]
+        time_oracle(osm.o, ks, sp, so, threads)
+    times = [time_oracle(osm.o, ks, sp, so, threads) for _ in range(args.steps)]
     total = sum(times)
     value = units * len(times) / total
     line = {
@@ -377,7 +426,7 @@ def run_reference(args):
         "query_bp_per_s": bp * len(times) / total,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{ks.size} k-mers + {so.size - 1} sequences per step "
-                                   f"({units} k-mers), restricted-mode index built in {build_s:.1f} s",
+                                   f"({units} k-mers), restricted-mode index built in {osm.build_s:.1f} s",
                          "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -519,9 +568,18 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     from paper_1910_04358_gb300 import rambo
 
+    t_start = time.time()
     corpus, kmers, q, desc = load_workload(args.workload)
     p = corpus.params
     n_seq_kmers, total_kmers, bp = batch_stats(p, kmers, q)
+    log(f"[bench] workload {args.workload} generated in {time.time() - t_start:.1f} s")
+    # the oracle's sample of this batch, built on host threads while the GPU
+    # sections run (rank 0 only); the timed answers are checked against it
+    osm = None
+    if rank == 0 and not args.no_oracle_check:
+        fk, fs = sample_fracs(args.workload)
+        osm = OracleSample(p, kmers, q, fk, fs)
+        osm.start(corpus, max(1, (os.cpu_count() or 1) - 2))
 
     def to_dev(a, dt):
         return torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
@@ -606,6 +664,9 @@ def run_ours(args):
     time.sleep(0.2)
     clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
+    # the timed steps' answers, kept for the oracle check
+    timed_k = out_k.clone() if out_k is not None else None
+    timed_s = out_s.clone()
     ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     prof = idx.profile_read()
@@ -732,10 +793,12 @@ def run_ours(args):
     kernel_ms = {k: (v["ms"] / (min(args.steps, 20)) if v["timed"] else None)
                  for k, v in prof_all.items()}
 
-    # ---- correctness spot check of the timed outputs against the host path
-    spot = min(q.n, 64)
-    host_chk = idx.query_seqs(q.packed, q.offsets[:spot + 1])
-    ok = bool(np.array_equal(rambo.as_u32(out_s[:spot]), host_chk))
+    # ---- the timed answers against the CPU oracle (sampled rows; rank 0)
+    log(f"[bench] GPU sections done at {time.time() - t_start:.1f} s; waiting for the oracle")
+    oracle_check = osm.check(timed_k, timed_s) if osm is not None else None
+    log(f"[bench] oracle check {oracle_check} at {time.time() - t_start:.1f} s")
+    del timed_k, timed_s
+    ok = oracle_check is None or bool(oracle_check["ok"])
 
     # ---- end to end through the host-buffer C ABI (H2D + D2H inside)
     e2e = None
@@ -762,6 +825,7 @@ def run_ours(args):
         e2e = {"value": total_kmers * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e, "steps": e2e_steps}
 
+    log(f"[bench] e2e done at {time.time() - t_start:.1f} s")
     # ---- serving: continuous batching on the same resident index
     serving = None
     if not args.no_serving and rank == 0:
@@ -770,28 +834,21 @@ def run_ours(args):
         except Exception as ex:  # report, do not hide
             serving = {"error": repr(ex)}
 
-    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    log(f"[bench] serving done at {time.time() - t_start:.1f} s")
+    # ---- CPU oracle baseline (rank 0, N = 1 only): the oracle as it stands,
+    # timed on the host cores on the checked sample
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and osm is not None and not osm.error:
         threads = os.cpu_count() or 1
-        fk, fs = (200, 100) if args.workload == "medium" else (1, 50)
-        o, ks, sp, so, obuild = oracle_sample(p, corpus, kmers, q, fk, fs, threads)
-        units = sample_kmers_count(p, ks, so)
+        units = sample_kmers_count(p, osm.ks, osm.s_offs)
         reps, spent = 0, 0.0
         while spent < 10.0 and reps < 200:
-            spent += time_oracle(o, ks, sp, so, threads)
+            spent += time_oracle(osm.o, osm.ks, osm.s_packed, osm.s_offs, threads)
             reps += 1
-        # one host thread on the same sample (a few repetitions)
-        reps1, spent1 = 0, 0.0
-        while spent1 < 3.0 and reps1 < 50:
-            spent1 += time_oracle(o, ks, sp, so, 1)
-            reps1 += 1
         cpu = {"value": units * reps / spent, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{ks.size} single k-mers + {so.size - 1} sequences ({units} k-mers) "
+               "sample": f"{osm.ks.size} single k-mers + {osm.s_offs.size - 1} sequences ({units} k-mers) "
                          f"x {reps} repetitions; restricted-mode oracle index "
-                         f"(tracks the sample's probe positions), built in {obuild:.1f} s",
-               "single_thread": {"value": units * reps1 / spent1, "unit": UNIT,
-                                 "repetitions": reps1},
+                         f"(tracks the sample's probe positions), built in {osm.build_s:.1f} s",
                "host": host_cpu()}
 
     clk = clocks.summary(t_wall0, t_wall1)
@@ -807,7 +864,7 @@ def run_ours(args):
         "build": {"seconds": build_s, "kmers": insert_kmers, "kmers_per_s": insert_kmers / build_s,
                   "insert_kernel_ms": prof_b["insert"]["ms"] or None,
                   "insert_mode": idx.get_tuning()["insert_mode"]},
-        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "spot_check_vs_host_api": ok,
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "oracle_check": oracle_check,
         "launch_mode": launch_mode, "eager_ms_per_step": ms_step_eager, "graph": graph,
         "tuning": idx.get_tuning(), "tuning_source": tuning_source, "serving": serving,
         "early_exit": early,
@@ -828,7 +885,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["medium", "large", "tiny", "stream"], default="medium")
+    ap.add_argument("--workload", choices=["medium", "large", "tiny", "stream"], default="large")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the CPU oracle check of the timed answers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -836,7 +895,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-early-exit", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=4000)
+    ap.add_argument("--serving-requests", type=int, default=20000)
     ap.add_argument("--query-path", type=int, default=None,
                     help="0 = prefix/probe/expand launches, 1 = persistent fused launch")
     args = ap.parse_args()

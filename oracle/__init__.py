@@ -85,6 +85,7 @@ def _load():
             "orc_word_position": (u64, [p, p, u64, u32]),
             "orc_insert_words": (C.c_int, [p, u32, p, p, u64]),
             "orc_query_words": (C.c_int, [p, p, p, u64, p]),
+            "orc_seq_positions": (C.c_int, [p, u64, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -92,6 +93,14 @@ def _load():
             f.argtypes = args
         _lib = lib
         return lib
+
+
+def _sorted_distinct(a) -> np.ndarray:
+    """Sorted distinct uint64 values (a sort and a neighbour compare)."""
+    a = np.sort(np.asarray(a, dtype=np.uint64).ravel())
+    if a.size:
+        a = a[np.concatenate(([True], a[1:] != a[:-1]))]
+    return np.ascontiguousarray(a)
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -155,7 +164,7 @@ class Rambo:
         if tracked is None:
             h = lib.orc_create(K, B, R, m, eta, k, seed)
         else:
-            t = np.ascontiguousarray(np.unique(np.asarray(tracked, dtype=np.uint64)))
+            t = _sorted_distinct(tracked)
             self._tracked = t
             h = lib.orc_create_restricted(K, B, R, m, eta, k, seed,
                                           _ptr(t) if t.size else None, t.size)
@@ -257,6 +266,25 @@ class Rambo:
     def probe_position(self, term: int, j: int) -> int:
         return int(_load().orc_probe_position(self._h, term, j))
 
+    def seq_positions(self, packed, offsets) -> np.ndarray:
+        """The eta probe positions of every k-mer of every sequence
+        [offsets[i], offsets[i+1]), in window order: shape (terms, eta)."""
+        packed = np.ascontiguousarray(packed, dtype=np.uint8)
+        offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+        L = np.diff(offs.astype(np.int64))
+        terms = int(np.maximum(L - self.k + 1, 0).sum())
+        out = np.zeros((max(terms, 1), self.eta), dtype=np.uint64)
+        if offs.size > 1:
+            _check(_load().orc_seq_positions(self._h, offs.size - 1, _ptr(packed), _ptr(offs),
+                                             _ptr(out)), "seq_positions")
+        return out[:terms]
+
+    def kmer_positions(self, kmers) -> np.ndarray:
+        """The eta probe positions of single k-mers given as forward codes."""
+        return np.array([[self.probe_position(canonical_of_code(int(x), self.k), j)
+                          for j in range(self.eta)] for x in np.asarray(kmers).tolist()],
+                        dtype=np.uint64).reshape(-1, self.eta)
+
     def filter_bit(self, r: int, b: int, pos: int) -> int:
         return int(_load().orc_filter_bit(self._h, r, b, pos))
 
@@ -272,6 +300,20 @@ class Rambo:
 
     def is_inserted(self, d: int) -> bool:
         return bool(_load().orc_is_inserted(self._h, d))
+
+
+def tracking_oracle(K, B, R, m, eta, k, seed, seqs=(), kmers=()) -> "Rambo":
+    """An empty restricted-mode oracle that tracks exactly the probe
+    positions of the given sequence batches ((packed, offsets) pairs) and
+    single k-mers (forward codes): exact for those queries."""
+    probe = Rambo(K, B, R, m, eta, k, seed, tracked=[0])
+    parts = [probe.seq_positions(pk, of).ravel() for pk, of in seqs]
+    km = np.asarray(kmers, dtype=np.uint64)
+    if km.size:
+        parts.append(probe.kmer_positions(km).ravel())
+    probe.close()
+    pos = _sorted_distinct(np.concatenate(parts)) if parts else np.zeros(0, np.uint64)
+    return Rambo(K, B, R, m, eta, k, seed, tracked=pos)
 
 
 def mask_to_docs(mask_words: np.ndarray) -> set[int]:

@@ -568,6 +568,29 @@ int orc_query_kmers(const orc_rambo *o, uint64_t n, const uint64_t *kmers, uint3
     return orc_query_many(o, n, NULL, NULL, kmers, out, n_threads);
 }
 
+/* The eta probe positions h_1(x)..h_eta(x) (Section 2.1) of every term x of
+ * every sequence i, Terms in window order (Section 3.3.1), written to
+ * pos[(first term of i + s) * eta + j].  `pos` holds eta * (total terms).
+ * Used to list the positions a restricted-mode oracle must track. */
+int orc_seq_positions(const orc_rambo *o, uint64_t n, const uint8_t *packed, const uint64_t *offs,
+                      uint64_t *pos) {
+    uint64_t at = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (offs[i + 1] < offs[i]) return ORC_EINVAL;
+        uint64_t n_bases = offs[i + 1] - offs[i];
+        if (n_bases < o->k) continue;
+        uint8_t *bases = (uint8_t *)malloc(n_bases);
+        if (!bases) return ORC_ENOMEM;
+        orc_unpack(packed, offs[i], n_bases, bases);
+        for (uint64_t s = 0; s + o->k <= n_bases; ++s) {
+            uint64_t x = orc_canonical_of_window(bases + s, o->k);
+            for (uint32_t j = 0; j < o->eta; ++j) pos[at++] = orc_probe_position(o, x, j);
+        }
+        free(bases);
+    }
+    return ORC_OK;
+}
+
 /* Explicit partition (Section 5.3 two-level routing: a stacked RAMBO uses
  * bucket b*tau(D) + phi(D)).  phi[d*R + r] < B; only before any insert. */
 int orc_set_partition(orc_rambo *o, const uint32_t *phi) {

@@ -362,6 +362,36 @@ def test_restricted_mode_matches_full_mode():
     assert np.array_equal(rs.query_seqs(q.packed, q.offsets), want)
 
 
+def test_bulk_positions_match_string_brute_force_and_tracking_oracle_is_exact():
+    # positions of every window: string-level canonical k-mer, then the pinned
+    # byte-string hash of its 8-byte code, first word mod m
+    p, corpus, q = _small_case(K=40, B=5, R=3, m=1 << 13)
+    o = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    got = o.seq_positions(q.packed, q.offsets)
+    want = []
+    for i in range(q.n):
+        s = _str(oracle.unpack(q.packed, int(q.offsets[i]), int(q.offsets[i + 1] - q.offsets[i])))
+        for t in range(len(s) - p.k + 1):
+            c = _code(_canon_str(s[t:t + p.k]))
+            want.append([oracle.mmh3_x64_128(c.to_bytes(8, "little"), p.seed + j)[0] % p.m
+                         for j in range(p.eta)])
+    assert got.shape == (len(want), p.eta) and got.tolist() == want
+    kmers = synth.sample_kmers(np.random.default_rng(3), corpus, 30, p.k, 0.5)
+    kp = o.kmer_positions(kmers)
+    for x, row in zip(kmers.tolist(), kp.tolist()):
+        s = "".join("ACGT"[(int(x) >> (2 * (p.k - 1 - i))) & 3] for i in range(p.k))
+        c = _code(_canon_str(s))
+        assert row == [oracle.mmh3_x64_128(c.to_bytes(8, "little"), p.seed + j)[0] % p.m
+                       for j in range(p.eta)]
+    # the tracking oracle answers those queries exactly as the full one
+    full = _build(p, corpus)
+    t = oracle.tracking_oracle(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed,
+                               seqs=[(q.packed, q.offsets)], kmers=kmers)
+    t.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets, threads=2)
+    assert np.array_equal(t.query_seqs(q.packed, q.offsets), full.query_seqs(q.packed, q.offsets))
+    assert np.array_equal(t.query_kmers(kmers), full.query_kmers(kmers))
+
+
 def test_invalid_arguments():
     with pytest.raises(oracle.OracleError):
         oracle.Rambo(0, 1, 1, 8, 1)
