@@ -308,8 +308,8 @@ typedef struct {
                                        /* expand launches; 1 = persistent fused launch */
                                        /* with length-bucketed work queues (groups up  */
                                        /* to 512 B; otherwise path 0 is used); 2 =     */
-                                       /* region-binned probing (groups up to 16 B and */
-                                       /* a workspace from                             */
+                                       /* region-binned probing (groups up to 64 B    */
+                                       /* and a workspace from                         */
                                        /* rambo_query_seqs_workspace_for; otherwise    */
                                        /* path 1)                                      */
     uint32_t fused_tile_kmers;         /* path 1: k-mers per tile of a long query      */
@@ -343,8 +343,9 @@ typedef struct {
     uint32_t bin_region_kib;           /* path 2: index bytes per region (KiB; 0 =     */
                                        /* 32768); regions hold a power-of-two number   */
                                        /* of groups and are at most 4096              */
-    uint32_t bin_rows;                 /* path 2: rows of 32 records a warp probes per */
-                                       /* work item (1, 2, 4 or 8; 0 = 2)              */
+    uint32_t bin_rows;                 /* path 2: group gathers a lane keeps in flight */
+                                       /* in the probe pass: 4, 6, 8 for 1, 2, 4 (and  */
+                                       /* 8); 0 = 1                                    */
     uint32_t host_direct;              /* host-buffer calls: 1 = kernels write answers */
                                        /* straight into output buffers that are        */
                                        /* page-locked and device-addressable (each     */

@@ -40,8 +40,8 @@ KNOBS = (
     ("probe_ctas_per_sm", (0, 1, 2, 4, 8)),
     ("kmer_async", (0, 1)),
     ("kmer_probe_ctas_per_sm", (0, 1, 2, 3, 4)),
-    ("bin_region_kib", (16384, 32768, 65536)),
-    ("bin_rows", (1, 2, 4, 8)),
+    ("bin_region_kib", (16384, 32768, 65536, 131072)),
+    ("bin_rows", (1, 2, 4)),
     ("fused_tile_kmers", (256, 512, 1024, 2048, 4096)),
     ("fused_short_max", (64, 256, 1024, 4096)),
     ("probe_min_kmers_per_warp", (0, 256, 1024, 4096)),
@@ -68,10 +68,10 @@ def _time(run, reps: int):
 def effective_path(tuning, info) -> int:
     """Sequence query path the library takes for this tuning and geometry (the
     binding always passes a workspace large enough for path 2): the binned
-    path for groups of at most 16 bytes, the fused path for groups of at most
+    path for groups of at most 64 bytes, the fused path for groups of at most
     512 bytes, else the separate launches."""
     g = info["group_bytes"]
-    if tuning["query_path"] == 2 and g <= 16:
+    if tuning["query_path"] == 2 and g <= 64:
         return 2
     if tuning["query_path"] >= 1 and g <= 512:
         return 1

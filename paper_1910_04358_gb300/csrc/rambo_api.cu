@@ -238,34 +238,37 @@ SeqWs seq_ws(const Geometry &g, uint64_t n) {
 
 size_t kmers_ws(const Geometry &g, uint64_t n) { return align_up(n * (uint64_t)g.Gw * 4); }
 
-// Extra workspace of the region-binned path (after the sequence layout): bin
-// counters, the work-item prefix and nb bins of cap records.  A bin holds
-// 1/8 more than its expected share of a batch whose k-mers are at most the
-// bases of packed_bytes (plus 1024), so with hashed positions records almost
-// never spill into the direct-probe path.
+// Extra workspace of the region-binned path (after the sequence layout):
+// the sub-bin counts, the tile -> query map and nb x G sub-bins of cap
+// records (G = the scatter's grid).  A sub-bin holds 1/8 more than its
+// expected share of a batch whose k-mers are at most the bases of
+// packed_bytes (plus 64), so with hashed positions records almost never
+// spill into the direct-probe path.
 struct BinLayout {
-    uint32_t nb, shift;
+    uint32_t nb, shift, G;
     uint64_t cap;
-    size_t count_off, pre_off, rec_off, bytes;
+    size_t count_off, tile_off, rec_off, bytes;
 };
-BinLayout bin_layout(const rambo_t *h, uint64_t packed_bytes) {
+BinLayout bin_layout(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
     const Geometry &g = h->g;
     BinLayout L{};
     const uint64_t region = (uint64_t)(h->tune.bin_region_kib ? h->tune.bin_region_kib : 32768) << 10;
     L.nb = binned_bins(g, region, &L.shift);
-    const uint64_t expect = (4 * packed_bytes * g.eta + L.nb - 1) / L.nb;
-    L.cap = expect + expect / 8 + 1024;
+    L.G = binned_scatter_grid(g, L.nb, h->sm_count);
+    const uint64_t subs = (uint64_t)L.nb * L.G;
+    const uint64_t expect = (4 * packed_bytes * g.eta + subs - 1) / subs;
+    L.cap = (expect + expect / 8 + 64 + 1) / 2 * 2;  // even: 16-byte aligned record pairs
     L.count_off = 0;
-    L.pre_off = align_up((size_t)L.nb * 8);
-    L.rec_off = L.pre_off + align_up(((size_t)L.nb + 1) * 8);
-    L.bytes = L.rec_off + (size_t)L.nb * L.cap * 8;
+    L.tile_off = align_up((size_t)subs * 4);
+    L.rec_off = L.tile_off + align_up((size_t)binned_max_tiles(g, n, packed_bytes) * 4);
+    L.bytes = L.rec_off + (size_t)subs * L.cap * 8;
     return L;
 }
 bool use_binned(const rambo_t *h) { return h->tune.query_path == 2 && binned_supported(h->g); }
 // Sequence workspace that lets the tuned path run on a batch over packed_bytes.
 size_t seq_ws_for(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
     size_t t = seq_ws(h->g, n).total;
-    if (use_binned(h)) t += bin_layout(h, packed_bytes).bytes;
+    if (use_binned(h)) t += bin_layout(h, n, packed_bytes).bytes;
     return t;
 }
 
@@ -332,16 +335,19 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     uint32_t *acc = reinterpret_cast<uint32_t *>(w + L.acc);
     const Aligned al = align_packed(packed, packed_bytes);
     if (use_binned(h)) {
-        const BinLayout B = bin_layout(h, packed_bytes);
+        const BinLayout B = bin_layout(h, n, packed_bytes);
         if (ws_bytes >= L.total + B.bytes) {
             // region-binned probing: records binned by index region, probed
             // region by region (L2 holds a region), then the expansion
+            BinnedArgs ba{};
+            ba.tile = binned_tile_kmers(g);
             {
+                // tile prefix: every query's k-mers in tiles of ba.tile
                 StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
-                RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
+                RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s,
+                                             ba.tile, 0));
             }
             RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
-            BinnedArgs ba{};
             ProbeArgs &a = ba.p;
             a.index = h->d_index;
             a.m = g.m;
@@ -360,13 +366,16 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
             a.acc = acc;
             a.err = h->d_err;
             char *bw = w + L.total;
-            ba.bin_count = reinterpret_cast<unsigned long long *>(bw + B.count_off);
-            ba.chunk_pre = reinterpret_cast<uint64_t *>(bw + B.pre_off);
+            ba.sub_count = reinterpret_cast<uint32_t *>(bw + B.count_off);
             ba.records = reinterpret_cast<uint64_t *>(bw + B.rec_off);
+            ba.tile_q = reinterpret_cast<uint32_t *>(bw + B.tile_off);
+            ba.max_tiles = binned_max_tiles(g, n, packed_bytes);
             ba.cap = B.cap;
             ba.nb = B.nb;
             ba.shift = B.shift;
-            ba.rows = h->tune.bin_rows ? h->tune.bin_rows : 2;
+            ba.G = B.G;
+            ba.depth = binned_depth(h->tune.bin_rows);
+            ba.cps = (uint32_t)((B.cap + BINNED_ITEM_RECS - 1) / BINNED_ITEM_RECS);
             {
                 StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, binned_launches());
                 RAMBO_TRY(launch_binned(ba, g, h->sm_count, s));

@@ -291,23 +291,37 @@ struct FusedQueues {
     uint32_t async;          // 1: one-lane 16-byte groups gathered into shared memory (cp.async)
 };
 bool fused_supported(const Geometry &g);
-// Region-binned probing of a sequence batch (query path 2, groups of at most
-// 16 bytes): bins of `cap` records each, region = pos >> shift.
+// Region-binned probing of a sequence batch (query path 2; groups of up to
+// 64 bytes): records in nb x G sub-bins of cap records each (bin = region
+// pos >> shift, G = the scatter's grid: one sub-bin per bin and block).
+constexpr uint32_t BINNED_TILE_RECS = 4096;  // probe records per scatter tile
+constexpr uint32_t BINNED_ITEM_RECS = 256;   // records per probe-pass work item
 struct BinnedArgs {
-    ProbeArgs p;                    // index, hashing, batch, kcum; acc preset to all ones
-    uint64_t *records;              // nb * cap records (group << 32 | query)
-    unsigned long long *bin_count;  // nb: records offered to each bin
-    uint64_t *chunk_pre;            // nb + 1: prefix of the probe pass's work items
-    uint64_t cap;                   // record slots per bin
+    ProbeArgs p;                    // index, hashing, batch; kcum = the tile prefix
+                                    // (tiles of `tile` k-mers, every query with k-mers);
+                                    // acc preset to all ones
+    uint64_t *records;              // nb * G * cap records (group << 32 | query)
+    uint32_t *sub_count;            // nb * G: records in each sub-bin (at most cap)
+    uint32_t *tile_q;               // query of each of the first max_tiles scatter tiles
+    uint64_t max_tiles;             // binned_max_tiles
+    uint64_t cap;                   // record slots per sub-bin (even)
     uint32_t nb, shift;
-    uint32_t rows;                  // probe pass: rows of 32 records per work item (1, 2, 4, 8)
+    uint32_t G;                     // scatter grid (binned_scatter_grid)
+    uint32_t tile;                  // k-mers per scatter tile (binned_tile_kmers)
+    uint32_t depth;                 // probe pass: gathers a lane keeps in flight (4, 6, 8)
+    uint32_t cps;                   // work items per sub-bin: ceil(cap / BINNED_ITEM_RECS)
 };
 bool binned_supported(const Geometry &g);
+uint32_t binned_tile_kmers(const Geometry &g);
+uint32_t binned_depth(uint32_t rows);  // from the bin_rows knob
+uint64_t binned_max_tiles(const Geometry &g, uint64_t n, uint64_t packed_bytes);
+uint32_t binned_scatter_grid(const Geometry &g, uint32_t nb, int sm_count);
 // Regions of (at most) region_bytes, a power-of-two number of groups, and at
 // most 4096 of them: returns the bin count, *shift = log2(groups per region).
 uint32_t binned_bins(const Geometry &g, uint64_t region_bytes, uint32_t *shift);
 int binned_launches();
 cudaError_t launch_binned(const BinnedArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
+
 // p.acc is unused (the bucket masks of long queries are e.acc).
 cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry &g,
                          const FusedQueues &qs, int grid_override, int sm_count, cudaStream_t s);

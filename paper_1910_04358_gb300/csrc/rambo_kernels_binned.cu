@@ -1,269 +1,358 @@
 // rambo_kernels_binned.cu -- region-binned probing of a sequence batch
 // (query path 2; the membership tests of Algorithm 2, Section 3.3.1).
 //
-// The flat and fused probes read one random position group per probe.  With
-// groups of at most 16 bytes every probe costs a whole 128-byte DRAM line, and
-// over a batch the same line is fetched again and again, because the index is
-// far larger than L2.  Here the probes of a batch are first binned by index
-// region (a power-of-two number of groups spanning about 32 MiB):
-//   scatter  every k-mer is extracted and hashed once; each probe becomes a
-//            record (group, query) in its region's bin.  A block stages a
-//            tile of records with their ranks in a shared-memory histogram,
-//            reserves each bin's run with one atomicAdd on the bin's counter
-//            and writes every record to its slot.  A record that finds its
-//            bin's share of the workspace full is probed on the spot.
-//   chunks   one block turns the bin counts into a prefix of work items.
-//   probe    warps take the work items in region order, so at any moment the
-//            grid probes inside one or two regions that fit in L2 and each
-//            line comes from DRAM about once per batch.
+// The flat and fused probes read one random position group per probe.  A
+// random read of at most 128 bytes costs a whole 128-byte DRAM line, and over
+// a batch the same line is fetched again and again, because the index is far
+// larger than L2: with 16-byte groups a probe uses an eighth of the line it
+// pays for, with 64-byte groups half of it.  Here the probes of a batch are
+// first binned by index region (a power-of-two number of groups spanning a
+// few tens of MiB), then probed region by region:
+//   scatter  a block takes one tile at a time: up to `tile` consecutive
+//            k-mers of ONE query (the tile prefix numbers every query's
+//            tiles).  Its threads extract and hash the k-mers and append
+//            every probe as a record (group, query) to the block's own
+//            sub-bin of the probe's region, the slot taken from a per-block
+//            cursor in shared memory: no global atomics, and the records a
+//            tile adds to a sub-bin are one run of one query.  A record that
+//            finds its sub-bin full is probed on the spot.
+//   probe    work items are fixed chunks of sub-bins in region-major order,
+//            so at any moment the grid probes inside about one region that
+//            fits in L2, and each line comes from DRAM about once per batch.
+//            A lane walks consecutive records, ANDing the groups of a run in
+//            registers (the gathers staged in shared memory by cp.async, a
+//            few records ahead); a closed run is folded into its query's mask
+//            by one coalesced atomicAnd per 64 bytes.
 // The per-query result does not depend on the order of the probes (a BFU
 // passes a query iff every probe of every k-mer finds its bit, so the bucket
-// mask is the AND of all probed groups); records of the same query are ANDed
-// within a warp and folded into the query's mask with atomicAnd.
+// mask is the AND of all probed groups), and neither does the sub-bin layout.
 #include "rambo_query_common.cuh"
 
 namespace rgpu {
 namespace {
 
+constexpr int SCATTER_THREADS = 512;
 constexpr int BIN_THREADS = 256;
-constexpr uint32_t BIN_TILE_RECS = 2048;  // probe records staged per block tile
-constexpr uint64_t BIN_MAX = 4096;        // most bins (index regions) per batch
+constexpr uint64_t BIN_MAX = 4096;   // most bins (index regions) per batch
 
 __device__ __forceinline__ uint64_t make_rec(uint32_t pos, uint32_t q) {
     return ((uint64_t)pos << 32) | q;
 }
 
-// Exclusive prefix (64-bit) of n values by one block; in place allowed when
-// in and out are the same 64-bit array (each thread reads its own segment
-// before writing it).  Returns the total to every thread.
-template <typename TI>
-__device__ uint64_t block_excl_scan(const TI *in, uint64_t *out, uint32_t n) {
-    __shared__ uint64_t warp_tot[BIN_THREADS / 32];
-    const uint32_t per = (n + BIN_THREADS - 1) / BIN_THREADS;
+// A probe whose sub-bin is full: its group ANDed into the query's mask directly.
+template <int SW>
+__device__ __forceinline__ void probe_direct(const ProbeArgs &p, uint32_t pos, uint32_t q) {
+    for (uint32_t w = 0; w < p.Gw; w += SW) {
+        const Slice<SW> v = ld_slice<SW>(p.index + (uint64_t)pos * p.Gw + w);
+        flush_slice<SW>(p.acc, q, p.Gw, w, v);
+    }
+}
+
+// tile_q[t] = the query whose k-mers tile t covers (one thread per query),
+// for the first max_tiles tiles (ranges may overlap, so a batch can have
+// more tiles than its packed bytes suggest; those are looked up by search).
+__global__ void k_bin_tiles(BinnedArgs a) {
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.p.n) return;
+    const uint64_t t1 = a.p.kcum[q + 1] < a.max_tiles ? a.p.kcum[q + 1] : a.max_tiles;
+    for (uint64_t t = a.p.kcum[q]; t < t1; ++t) a.tile_q[t] = (uint32_t)q;
+}
+
+// First k-mer, end and start base of tile t.
+struct TileHead {
+    uint64_t k0, k1, start;
+    uint32_t q;
+};
+__device__ __forceinline__ TileHead tile_head(const BinnedArgs &a, uint64_t t) {
+    const ProbeArgs &p = a.p;
+    TileHead h;
+    h.q = t < a.max_tiles ? a.tile_q[t] : (uint32_t)find_query(p.kcum, p.n, t);
+    const uint64_t b0 = p.offsets[h.q], b1 = p.ends[h.q];
+    const uint64_t nk = b1 - b0 - p.k + 1;  // the prefix counted only items with k-mers
+    h.k0 = (t - p.kcum[h.q]) * a.tile;
+    h.k1 = h.k0 + a.tile < nk ? h.k0 + a.tile : nk;
+    h.start = b0 + p.base_shift;
+    return h;
+}
+
+// Exclusive prefix of n 32-bit counts in shared memory, in place, by the
+// whole block (n up to a few thousand); every thread returns after the
+// prefix is written.
+__device__ void block_scan_counts(uint32_t *v, uint32_t n) {
+    __shared__ uint32_t warp_tot[SCATTER_THREADS / 32];
+    const uint32_t per = (n + SCATTER_THREADS - 1) / SCATTER_THREADS;
     const uint32_t b0 = threadIdx.x * per;
-    uint64_t sum = 0;
+    uint32_t sum = 0;
     for (uint32_t i = 0; i < per; ++i)
-        if (b0 + i < n) sum += in[b0 + i];
+        if (b0 + i < n) sum += v[b0 + i];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint64_t incl = sum;
+    uint32_t incl = sum;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const uint64_t y = __shfl_up_sync(FULL, incl, off);
+        const uint32_t y = __shfl_up_sync(FULL, incl, off);
         if (lane >= off) incl += y;
     }
     if (lane == 31) warp_tot[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        uint64_t v = lane < BIN_THREADS / 32 ? warp_tot[lane] : 0;
+        uint32_t x = lane < SCATTER_THREADS / 32 ? warp_tot[lane] : 0;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const uint64_t y = __shfl_up_sync(FULL, v, off);
-            if (lane >= off) v += y;
+            const uint32_t y = __shfl_up_sync(FULL, x, off);
+            if (lane >= off) x += y;
         }
-        if (lane < BIN_THREADS / 32) warp_tot[lane] = v;  // inclusive over warps
+        if (lane < SCATTER_THREADS / 32) warp_tot[lane] = x;
     }
     __syncthreads();
-    uint64_t run = (wid ? warp_tot[wid - 1] : 0) + incl - sum;
-    const uint64_t total = warp_tot[BIN_THREADS / 32 - 1];
+    uint32_t run = (wid ? warp_tot[wid - 1] : 0) + incl - sum;
     for (uint32_t i = 0; i < per; ++i) {
         if (b0 + i < n) {
-            const uint64_t v = (uint64_t)in[b0 + i];
-            out[b0 + i] = run;
-            run += v;
+            const uint32_t x = v[b0 + i];
+            v[b0 + i] = run;
+            run += x;
         }
     }
-    __syncthreads();
-    return total;
 }
 
-template <int SW>
-__global__ void __launch_bounds__(BIN_THREADS) k_bin_scatter(BinnedArgs a) {
-    extern __shared__ uint64_t smem64[];
-    uint64_t *s_rec = smem64;                                        // BIN_TILE_RECS, tile order
-    uint64_t *s_base = s_rec + BIN_TILE_RECS;                        // nb: first slot of the tile's run
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_base + a.nb);  // nb: records per bin
-    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_hist + a.nb);  // BIN_TILE_RECS
-    __shared__ uint64_t s_qa[BIN_THREADS], s_qb[BIN_THREADS];
+__host__ __device__ inline size_t scatter_smem(uint32_t nb, uint32_t tile_recs) {
+    // per bin: two count / offset arrays (alternate tiles), sub-bin cursor,
+    // cursor before the tile; per record: group, group in bin order, rank
+    return (size_t)nb * 16 + (size_t)tile_recs * 10;
+}
 
+// Scatter.  Sub-bin (b, blk) of the records is b * G + blk.  Per tile:
+//   1  extract and hash the k-mers; count the tile's probes per bin (rank)
+//   2  prefix of the counts = the tile's records in bin order; the block's
+//      sub-bin cursors advance by the counts
+//   3  the records in bin order in shared memory
+//   4  written out in that order, so the lanes of a warp store a few whole
+//      runs (consecutive slots of one sub-bin) instead of 32 scattered
+//      records; the other count array is cleared for the next tile
+template <int SW>
+__global__ void __launch_bounds__(SCATTER_THREADS) k_bin_scatter(BinnedArgs a) {
+    extern __shared__ uint32_t smem32[];
+    uint32_t *s_cnt2 = smem32;                       // 2 x nb: tile counts, then tile offsets
+    uint32_t *s_cursor = s_cnt2 + 2 * a.nb;          // nb: the block's records per sub-bin
+    uint32_t *s_gbase = s_cursor + a.nb;             // nb: cursor before this tile
+    const uint32_t TR = a.tile * a.p.eta;
+    uint32_t *s_pos = s_gbase + a.nb;                // TR
+    uint32_t *s_sorted = s_pos + TR;                 // TR
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_sorted + TR);  // TR
+    __shared__ TileHead s_head[2];
     const ProbeArgs &p = a.p;
-    const uint64_t T = p.kcum[p.n];
-    const uint32_t kpt = BIN_TILE_RECS / p.eta;  // k-mers per tile
-    const uint64_t tiles = (T + kpt - 1) / kpt;
-    for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) s_hist[b] = 0;
-    // this block's tiles are blockIdx.x + i * gridDim.x; their query ranges
-    // are looked up BIN_THREADS tiles at a time, one tile per thread
-    for (uint64_t i0 = 0; blockIdx.x + i0 * gridDim.x < tiles; i0 += BIN_THREADS) {
-        {
-            const uint64_t tile = blockIdx.x + (i0 + threadIdx.x) * gridDim.x;
-            if (tile < tiles) {
-                const uint64_t t0 = tile * kpt, t1 = t0 + kpt < T ? t0 + kpt : T;
-                s_qa[threadIdx.x] = find_query(p.kcum, p.n, t0);
-                s_qb[threadIdx.x] = find_query(p.kcum, p.n, t1 - 1);
+    const uint64_t tiles = p.kcum[p.n];  // the tile prefix
+    for (uint32_t b = threadIdx.x; b < 2 * a.nb; b += SCATTER_THREADS) s_cnt2[b] = 0;
+    for (uint32_t b = threadIdx.x; b < a.nb; b += SCATTER_THREADS) s_cursor[b] = 0;
+    if (threadIdx.x == 0 && blockIdx.x < tiles) s_head[0] = tile_head(a, blockIdx.x);
+    __syncthreads();
+    unsigned long long *rec = reinterpret_cast<unsigned long long *>(a.records);
+    uint32_t parity = 0;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x, parity ^= 1u) {
+        uint32_t *s_cnt = s_cnt2 + parity * a.nb;
+        uint32_t *s_other = s_cnt2 + (parity ^ 1u) * a.nb;
+        const TileHead h = s_head[parity];
+        TileHead nxt{};
+        const bool has_next = t + gridDim.x < tiles;
+        if (threadIdx.x == 0 && has_next) nxt = tile_head(a, t + gridDim.x);  // in flight during 1
+        // 1
+        for (uint64_t g = h.k0 + threadIdx.x; g < h.k1; g += SCATTER_THREADS) {
+            const uint64_t c = canonical_from_window(base_window(p.packed, p.packed_bytes, h.start + g), p.k);
+            const uint64_t km = mh_mix_key(c);
+            const uint32_t r0 = (uint32_t)(g - h.k0) * p.eta;
+            for (uint32_t j = 0; j < p.eta; ++j) {
+                const uint32_t pos = reduce_pos(mh_first_word(km, p.seed32 + j), p.m, p.m_pow2);
+                s_pos[r0 + j] = pos;
+                s_rank[r0 + j] = (uint16_t)atomicAdd(&s_cnt[pos >> a.shift], 1u);
             }
+        }
+        if (threadIdx.x == 0 && has_next) s_head[parity ^ 1u] = nxt;
+        __syncthreads();
+        // 2
+        for (uint32_t b = threadIdx.x; b < a.nb; b += SCATTER_THREADS) {
+            s_gbase[b] = s_cursor[b];
+            s_cursor[b] += s_cnt[b];
+        }
+        block_scan_counts(s_cnt, a.nb);
+        __syncthreads();
+        // 3
+        const uint32_t nrec = (uint32_t)(h.k1 - h.k0) * p.eta;
+        for (uint32_t r = threadIdx.x; r < nrec; r += SCATTER_THREADS) {
+            const uint32_t pos = s_pos[r];
+            s_sorted[s_cnt[pos >> a.shift] + s_rank[r]] = pos;
         }
         __syncthreads();
-        for (uint32_t i = 0; i < BIN_THREADS; ++i) {
-            const uint64_t tile = blockIdx.x + (i0 + i) * gridDim.x;
-            if (tile >= tiles) break;
-            const uint64_t t0 = tile * kpt;
-            const uint64_t t1 = t0 + kpt < T ? t0 + kpt : T;
-            const uint64_t qa = s_qa[i], qb = s_qb[i];
-            // phase 1: k-mers of the tile -> records; rank within the bin's run
-            for (uint64_t g = t0 + threadIdx.x; g < t1; g += BIN_THREADS) {
-                uint64_t lo = qa, hi = qb + 1;
-                while (hi - lo > 1) {
-                    const uint64_t mid = (lo + hi) >> 1;
-                    if (p.kcum[mid] <= g) lo = mid;
-                    else hi = mid;
-                }
-                const uint64_t start = p.offsets[lo] + p.base_shift + (g - p.kcum[lo]);
-                const uint64_t c = canonical_from_window(base_window(p.packed, p.packed_bytes, start), p.k);
-                const uint64_t km = mh_mix_key(c);
-                const uint32_t r0 = (uint32_t)(g - t0) * p.eta;
-                for (uint32_t j = 0; j < p.eta; ++j) {
-                    const uint32_t pos = reduce_pos(mh_first_word(km, p.seed32 + j), p.m, p.m_pow2);
-                    s_rec[r0 + j] = make_rec(pos, (uint32_t)lo);
-                    s_rank[r0 + j] = (uint16_t)atomicAdd(&s_hist[pos >> a.shift], 1u);
-                }
-            }
-            __syncthreads();
-            // phase 2: reserve every bin's run once
-            for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) {
-                const uint32_t cnt = s_hist[b];
-                s_base[b] = cnt ? atomicAdd(a.bin_count + b, (unsigned long long)cnt) : 0ull;
-            }
-            __syncthreads();
-            // phase 3: every record to its slot (the bin's share full: probe it now)
-            const uint32_t nrec = (uint32_t)(t1 - t0) * p.eta;
-            for (uint32_t r = threadIdx.x; r < nrec; r += BIN_THREADS) {
-                const uint64_t rec = s_rec[r];
-                const uint32_t pos = (uint32_t)(rec >> 32), q = (uint32_t)rec;
-                const uint32_t b = pos >> a.shift;
-                const uint64_t slot = s_base[b] + s_rank[r];
-                if (slot < a.cap) {
-                    __stcs(reinterpret_cast<unsigned long long *>(a.records) + (uint64_t)b * a.cap + slot,
-                           (unsigned long long)rec);
-                } else {
-                    const Slice<SW> v = ld_slice<SW>(p.index + (uint64_t)pos * p.Gw);
-                    flush_slice<SW>(p.acc, q, p.Gw, 0, v);
-                }
-            }
-            for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) s_hist[b] = 0;
-            __syncthreads();
+        // 4
+        for (uint32_t i = threadIdx.x; i < nrec; i += SCATTER_THREADS) {
+            const uint32_t pos = s_sorted[i];
+            const uint32_t b = pos >> a.shift;
+            const uint32_t slot = s_gbase[b] + (i - s_cnt[b]);
+            if (slot < a.cap)
+                __stcs(rec + ((uint64_t)b * gridDim.x + blockIdx.x) * a.cap + slot,
+                       (unsigned long long)make_rec(pos, h.q));
+            else
+                probe_direct<SW>(p, pos, h.q);
         }
+        for (uint32_t b = threadIdx.x; b < a.nb; b += SCATTER_THREADS) s_other[b] = 0;
+        __syncthreads();
+    }
+    for (uint32_t b = threadIdx.x; b < a.nb; b += SCATTER_THREADS)
+        a.sub_count[(uint64_t)b * gridDim.x + blockIdx.x] = s_cursor[b] < a.cap ? s_cursor[b] : (uint32_t)a.cap;
+}
+
+// ANDs a run's slice into the query's bucket mask: 64-bit atomics for
+// 16-byte slices (the mask rows are 8-byte aligned), all-ones words skipped.
+// The L lanes of a group flush its L slices in one instruction: a coalesced
+// reduction over the query's whole mask row.
+template <int SW>
+__device__ __forceinline__ void flush_run(uint32_t *acc, uint32_t q, uint32_t Gw, uint32_t word0,
+                                          const Slice<SW> &v) {
+    if constexpr (SW == 4) {
+        unsigned long long *p = reinterpret_cast<unsigned long long *>(acc + (uint64_t)q * Gw + word0);
+        const unsigned long long lo = ((unsigned long long)v.w[1] << 32) | v.w[0];
+        const unsigned long long hi = ((unsigned long long)v.w[3] << 32) | v.w[2];
+        if (lo != ~0ull) atomicAnd(p, lo);
+        if (hi != ~0ull) atomicAnd(p + 1, hi);
+    } else {
+        flush_slice<SW>(acc, q, Gw, word0, v);
     }
 }
 
-// One block: chunk_pre[b] = exclusive prefix over bins of their work items,
-// chunk_pre[nb] = total.
-__global__ void __launch_bounds__(BIN_THREADS) k_bin_chunks(BinnedArgs a) {
-    const uint32_t chunk = 32u * a.rows;
-    for (uint32_t b = threadIdx.x; b < a.nb; b += BIN_THREADS) {
-        const uint64_t cnt = a.bin_count[b] < a.cap ? a.bin_count[b] : a.cap;
-        a.chunk_pre[b] = (cnt + chunk - 1) / chunk;
-    }
-    __syncthreads();
-    const uint64_t total = block_excl_scan(a.chunk_pre, a.chunk_pre, a.nb);
-    if (threadIdx.x == 0) a.chunk_pre[a.nb] = total;
-}
-
-// U rows of 32 records per warp work item; the grid's work items in flight
-// span U * 32 * (warps) records, which should stay within about one region.
-template <int SW, int BIN_U>
+// Probe pass.  A group of GW words is read by L = GW/4 lanes (one lane for
+// groups of up to 16 bytes), 16 bytes each; a warp has 32/L lane groups.
+// Work item c = chunk (c % cps) of sub-bin (c / cps): 256 consecutive
+// records; lane group j walks its 256/(32/L) consecutive records of it in
+// order, keeping the AND of the current run (records of one query) in
+// registers, with the gathers of the next D records in flight.  A run is
+// folded into its query's mask where the query changes and at the end of
+// the walk.
+template <int GW, int D>
 __global__ void __launch_bounds__(BIN_THREADS) k_bin_probe(BinnedArgs a) {
-    constexpr uint32_t BIN_CHUNK = 32u * BIN_U;
+    constexpr int L = GW >= 4 ? GW / 4 : 1;   // lanes per group
+    constexpr int SW = GW >= 4 ? 4 : GW;      // words per lane
+    constexpr int PERG = BINNED_ITEM_RECS / (32 / L);  // records per lane group and item
+    constexpr int RPL = PERG / L;             // records each lane loads (8)
     const int lane = threadIdx.x & 31;
+    const int grp = lane / L, sub = lane % L;
+    const uint32_t word0 = (uint32_t)sub * SW;
     const uint64_t warp = (uint64_t)blockIdx.x * (BIN_THREADS / 32) + (threadIdx.x >> 5);
     const uint64_t nwarps = (uint64_t)gridDim.x * (BIN_THREADS / 32);
-    const uint64_t total = a.chunk_pre[a.nb];
-    const uint32_t Gw = a.p.Gw;
-    for (uint64_t c = warp; c < total; c += nwarps) {
-        // bin holding work item c: largest b with chunk_pre[b] <= c
-        uint32_t lo = 0, hi = a.nb;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (a.chunk_pre[mid] <= c) lo = mid;
-            else hi = mid;
-        }
-        const uint64_t cnt = a.bin_count[lo] < a.cap ? a.bin_count[lo] : a.cap;
-        const uint64_t off = (c - a.chunk_pre[lo]) * BIN_CHUNK;
+    const uint64_t items = (uint64_t)a.nb * a.G * a.cps;
+    uint32_t *acc = a.p.acc;
+    const uint32_t *index = a.p.index;
+    for (uint64_t c = warp; c < items; c += nwarps) {
+        const uint64_t sb = c / a.cps;
+        const uint32_t cnt = a.sub_count[sb];
+        const uint32_t chunk0 = (uint32_t)(c - sb * a.cps) * BINNED_ITEM_RECS;
+        if (chunk0 >= cnt) continue;  // warp-uniform: an empty chunk
+        const uint32_t gfirst = chunk0 + (uint32_t)grp * PERG;
+        const uint32_t ng = gfirst < cnt ? (cnt - gfirst < (uint32_t)PERG ? cnt - gfirst : (uint32_t)PERG) : 0u;
         const unsigned long long *rec =
-            reinterpret_cast<const unsigned long long *>(a.records) + (uint64_t)lo * a.cap;
-        uint64_t r[BIN_U];
+            reinterpret_cast<const unsigned long long *>(a.records) + sb * a.cap + gfirst;
+        // this lane's share of the group's records: sub, sub + L, ...
+        unsigned long long r[RPL];
 #pragma unroll
-        for (int u = 0; u < BIN_U; ++u) {
-            const uint64_t i = off + (uint64_t)u * 32 + lane;
-            r[u] = i < cnt ? __ldcs(rec + i) : ~0ull;
+        for (int k = 0; k < RPL; ++k) {
+            const uint32_t i = (uint32_t)(sub + L * k);
+            r[k] = i < ng ? __ldcs(rec + i) : ~0ull;
         }
-        Slice<SW> v[BIN_U];
+        // record i of the group, seen by all of its lanes
+        auto rec_at = [&](int i) -> unsigned long long {
+            return __shfl_sync(FULL, r[i / L], grp * L + i % L);
+        };
+        Slice<SW> buf[D];
 #pragma unroll
-        for (int u = 0; u < BIN_U; ++u) {
-            if (r[u] != ~0ull) v[u] = ld_slice<SW>(a.p.index + (r[u] >> 32) * Gw);
-            else slice_ones(v[u]);
+        for (int i = 0; i < D; ++i) {
+            const unsigned long long x = rec_at(i);
+            if (i < PERG && x != ~0ull) buf[i] = ld_slice<SW>(index + (x >> 32) * GW + word0);
+            else slice_ones(buf[i]);
         }
-        // AND the records of each query present in a row, one atomic per word
+        uint32_t cq = NONE;
+        Slice<SW> run;
+        slice_ones(run);
 #pragma unroll
-        for (int u = 0; u < BIN_U; ++u) {
-            const uint32_t q = r[u] != ~0ull ? (uint32_t)r[u] : NONE;
-            uint32_t todo = __ballot_sync(FULL, q != NONE);
-            while (todo) {
-                const int l = __ffs(todo) - 1;
-                const uint32_t qq = __shfl_sync(FULL, q, l);
-                const bool mine = q == qq;
-                todo &= ~__ballot_sync(FULL, mine);
-#pragma unroll
-                for (int w = 0; w < SW; ++w) {
-                    const uint32_t x = __reduce_and_sync(FULL, mine ? v[u].w[w] : FULL);
-                    if (lane == l && x != FULL) atomicAnd(a.p.acc + (uint64_t)qq * Gw + w, x);
-                }
+        for (int i = 0; i < PERG; ++i) {
+            const unsigned long long x = rec_at(i);
+            const uint32_t q = x != ~0ull ? (uint32_t)x : NONE;
+            if (q != cq) {
+                if (cq != NONE) flush_run<SW>(acc, cq, GW, word0, run);
+                cq = q;
+                slice_ones(run);
+            }
+            slice_and(run, buf[i % D]);
+            if (i + D < PERG) {
+                const unsigned long long y = rec_at(i + D);
+                if (y != ~0ull) buf[i % D] = ld_slice<SW>(index + (y >> 32) * GW + word0);
+                else slice_ones(buf[i % D]);
             }
         }
+        if (cq != NONE) flush_run<SW>(acc, cq, GW, word0, run);
     }
 }
 
-size_t scatter_smem(uint32_t nb) {
-    return (size_t)BIN_TILE_RECS * 8 + (size_t)nb * (8 + 4) + (size_t)BIN_TILE_RECS * 2;
+template <int GW, int D>
+cudaError_t launch_probe_d(const BinnedArgs &a, int sm_count, cudaStream_t s) {
+    int occ = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bin_probe<GW, D>, BIN_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    k_bin_probe<GW, D><<<(occ > 0 ? occ : 1) * sm_count, BIN_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int GW>
+cudaError_t launch_probe_pass(const BinnedArgs &a, int sm_count, cudaStream_t s) {
+    switch (a.depth) {
+        case 4: return launch_probe_d<GW, 4>(a, sm_count, s);
+        case 6: return launch_probe_d<GW, 6>(a, sm_count, s);
+        default: return launch_probe_d<GW, 8>(a, sm_count, s);
+    }
 }
 
 template <int SW>
-cudaError_t launch_binned_t(const BinnedArgs &a, int sm_count, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(a.bin_count, 0, (size_t)a.nb * 8, s);
-    if (e != cudaSuccess) return e;
-    const size_t smem = scatter_smem(a.nb);
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_bin_scatter<SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+int scatter_blocks_per_sm(size_t smem) {
+    // (always set: the kernel's static shared memory counts against the
+    // default 48 KB too)
+    if (cudaFuncSetAttribute(k_bin_scatter<SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 1;
     int occ = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bin_scatter<SW>, BIN_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    k_bin_scatter<SW><<<(occ > 0 ? occ : 1) * sm_count, BIN_THREADS, smem, s>>>(a);
-    k_bin_chunks<<<1, BIN_THREADS, 0, s>>>(a);
-    int occ_p = 1;
-#define RGPU_BIN_PROBE(U)                                                                          \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_bin_probe<SW, U>, BIN_THREADS, 0); \
-    if (e != cudaSuccess) return e;                                                                \
-    k_bin_probe<SW, U><<<(occ_p > 0 ? occ_p : 1) * sm_count, BIN_THREADS, 0, s>>>(a);
-    switch (a.rows) {
-        case 1: RGPU_BIN_PROBE(1) break;
-        case 2: RGPU_BIN_PROBE(2) break;
-        case 4: RGPU_BIN_PROBE(4) break;
-        default: RGPU_BIN_PROBE(8) break;
-    }
-#undef RGPU_BIN_PROBE
-    return cudaGetLastError();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bin_scatter<SW>, SCATTER_THREADS, smem) !=
+            cudaSuccess || occ < 1)
+        occ = 1;
+    return occ;
 }
 
 }  // namespace
 
-bool binned_supported(const Geometry &g) { return g.LPG == 1 && (g.Gw == 1 || g.Gw == 2 || g.Gw == 4); }
+bool binned_supported(const Geometry &g) { return g.Gw == 1 || g.Gw == 2 || g.Gw == 4 || g.Gw == 8 || g.Gw == 16; }
+
+uint32_t binned_records_per_item() { return BINNED_ITEM_RECS; }
+
+uint32_t binned_depth(uint32_t rows) { return (rows == 0 || rows == 1) ? 4u : rows == 2 ? 6u : 8u; }
+
+uint32_t binned_tile_kmers(const Geometry &g) {
+    const uint32_t t = BINNED_TILE_RECS / (g.eta ? g.eta : 1);
+    return t ? t : 1;
+}
+
+uint64_t binned_max_tiles(const Geometry &g, uint64_t n, uint64_t packed_bytes) {
+    // every query with k-mers has ceil(k-mers / tile) tiles, and its k-mers
+    // are at most its bases (queries' ranges may overlap: see k_bin_tiles)
+    return n + 4 * packed_bytes / binned_tile_kmers(g) + 1;
+}
+
+uint32_t binned_scatter_grid(const Geometry &g, uint32_t nb, int sm_count) {
+    const size_t smem = scatter_smem(nb, binned_tile_kmers(g) * g.eta);
+    const int occ = g.SW == 1 ? scatter_blocks_per_sm<1>(smem)
+                              : g.SW == 2 ? scatter_blocks_per_sm<2>(smem) : scatter_blocks_per_sm<4>(smem);
+    return (uint32_t)(occ * sm_count);
+}
 
 uint32_t binned_bins(const Geometry &g, uint64_t region_bytes, uint32_t *shift) {
     uint64_t region_groups = region_bytes / ((uint64_t)g.Gw * 4);
     if (region_groups == 0) region_groups = 1;
     uint32_t sh = 0;
     while ((1ull << (sh + 1)) <= region_groups) ++sh;
-    // at most BIN_MAX bins (the scatter's shared-memory histogram)
+    // at most BIN_MAX bins (the scatter's shared-memory cursors)
     while (((g.m + (1ull << sh) - 1) >> sh) > BIN_MAX) ++sh;
     *shift = sh;
     return (uint32_t)((g.m + (1ull << sh) - 1) >> sh);
@@ -272,10 +361,28 @@ uint32_t binned_bins(const Geometry &g, uint64_t region_bytes, uint32_t *shift) 
 int binned_launches() { return 3; }
 
 cudaError_t launch_binned(const BinnedArgs &a, const Geometry &g, int sm_count, cudaStream_t s) {
+    if (!binned_supported(g) || a.tile == 0 || (uint64_t)a.tile * a.p.eta > BINNED_TILE_RECS ||
+        a.nb == 0 || a.nb > BIN_MAX || a.G == 0 || (a.cap & 1) ||
+        (a.depth != 4 && a.depth != 6 && a.depth != 8) ||
+        a.cps != (uint32_t)((a.cap + BINNED_ITEM_RECS - 1) / BINNED_ITEM_RECS))
+        return cudaErrorInvalidValue;
+    if (a.p.n == 0) return cudaSuccess;
+    k_bin_tiles<<<(unsigned)((a.p.n + 255) / 256), 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = scatter_smem(a.nb, a.tile * a.p.eta);
+    switch (g.SW) {
+        case 1: scatter_blocks_per_sm<1>(smem); k_bin_scatter<1><<<a.G, SCATTER_THREADS, smem, s>>>(a); break;
+        case 2: scatter_blocks_per_sm<2>(smem); k_bin_scatter<2><<<a.G, SCATTER_THREADS, smem, s>>>(a); break;
+        default: scatter_blocks_per_sm<4>(smem); k_bin_scatter<4><<<a.G, SCATTER_THREADS, smem, s>>>(a); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     switch (g.Gw) {
-        case 1: return launch_binned_t<1>(a, sm_count, s);
-        case 2: return launch_binned_t<2>(a, sm_count, s);
-        default: return launch_binned_t<4>(a, sm_count, s);
+        case 1: return launch_probe_pass<1>(a, sm_count, s);
+        case 2: return launch_probe_pass<2>(a, sm_count, s);
+        case 4: return launch_probe_pass<4>(a, sm_count, s);
+        case 8: return launch_probe_pass<8>(a, sm_count, s);
+        default: return launch_probe_pass<16>(a, sm_count, s);
     }
 }
 

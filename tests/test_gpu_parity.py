@@ -461,19 +461,23 @@ def test_insert_modes_give_identical_index(rambo_lib, K, B, R, m):
 
 # ------------------------------------------------ region-binned probing (path 2)
 
-@pytest.mark.parametrize("K,B,R,m,region_kib", [
-    (200, 20, 3, 1 << 16, 64),          # 8-byte groups, 8 regions
-    (300, 32, 4, 1 << 18, 256),         # 16-byte groups, 16 regions
-    (64, 8, 2, (1 << 15) + 123, 16),    # 4-byte groups, m not a power of two, ragged last region
-    (300, 32, 4, 1 << 18, 0),           # default region size: one region
-    (150, 40, 4, 1 << 16, 64),          # 32-byte groups: path 2 unsupported, path 1 runs
+@pytest.mark.parametrize("K,B,R,m,eta,region_kib,max_len", [
+    (200, 20, 3, 1 << 16, 2, 64, 900),           # 8-byte groups, 8 regions
+    (300, 32, 4, 1 << 18, 2, 256, 900),          # 16-byte groups, 16 regions
+    (64, 8, 2, (1 << 15) + 123, 2, 16, 900),     # 4-byte groups, m not a power of two, ragged last region
+    (300, 32, 4, 1 << 18, 2, 0, 900),            # default region size: one region
+    (150, 40, 4, 1 << 16, 2, 64, 900),           # 32-byte groups (two lanes per group)
+    (300, 100, 5, 1 << 16, 2, 256, 12000),       # 64-byte groups; queries of up to three scatter tiles
+    (300, 100, 5, (1 << 16) + 77, 3, 128, 9000), # 64-byte groups, eta 3 (2730 k-mers a tile), odd m
+    (400, 200, 4, 1 << 15, 2, 512, 6000),        # 128-byte groups: path 2 unsupported, path 1 runs
 ])
-def test_binned_path_matches_oracle(rambo_lib, K, B, R, m, region_kib):
+def test_binned_path_matches_oracle(rambo_lib, K, B, R, m, eta, region_kib, max_len):
     torch = _torch()
-    p = synth.Params(K=K, B=B, R=R, m=m, eta=2, k=31, seed=9)
+    p = synth.Params(K=K, B=B, R=R, m=m, eta=eta, k=31, seed=9)
     rng = np.random.default_rng(K + B)
-    corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=1500, sub_rate=0.01)
-    q = synth.sample_queries(rng, corpus, rng.integers(0, 900, size=300), 0.5)
+    corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=max(1500, max_len + 100), sub_rate=0.01)
+    # lengths from empty to several tiles; whole documents among the sources
+    q = synth.sample_queries(rng, corpus, rng.integers(0, max_len, size=300), 0.5)
     o = oracle_index(p, corpus)
     want = o.query_seqs(q.packed, q.offsets)
     idx = gpu_index(rambo_lib, p, corpus)
@@ -490,12 +494,16 @@ def test_binned_path_matches_oracle(rambo_lib, K, B, R, m, region_kib):
     assert np.array_equal(rambo_lib.as_u32(out), want)
 
 
-def test_binned_path_overflow_probes_directly(rambo_lib):
-    # 2,000 queries over the same 1,500 bases: ten times more probe records
-    # than the packed bytes bound the bins for, so most are probed on the spot
-    p = synth.Params(K=100, B=16, R=3, m=1 << 16, eta=2, k=31, seed=3)
+@pytest.mark.parametrize("B,R,doc_len", [(16, 3, 1500), (100, 5, 1500), (100, 5, 9000)])
+def test_binned_path_overflow_probes_directly(rambo_lib, B, R, doc_len):
+    # 2,000 queries over the same document: ten times more probe records than
+    # the packed bytes bound the bins for, so most are probed on the spot
+    # (16- and 64-byte groups); with 9,000 bases every query has three
+    # scatter tiles, more than the tile map holds, so later tiles find their
+    # query by search
+    p = synth.Params(K=100, B=B, R=R, m=1 << 16, eta=2, k=31, seed=3)
     rng = np.random.default_rng(77)
-    corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=1500, sub_rate=0.01)
+    corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=doc_len, sub_rate=0.01)
     o = oracle_index(p, corpus)
     b0, b1 = int(corpus.offsets[7]), int(corpus.offsets[8])
     one = o.query_seqs(corpus.packed, np.array([b0, b1], dtype=np.uint64))

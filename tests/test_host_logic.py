@@ -20,7 +20,9 @@ def test_bench_effective_path():
     import bench
     t = lambda qp: {"query_path": qp}
     assert bench.effective_path(t(2), {"group_bytes": 16}) == 2
-    assert bench.effective_path(t(2), {"group_bytes": 64}) == 1
+    assert bench.effective_path(t(2), {"group_bytes": 64}) == 2
+    assert bench.effective_path(t(2), {"group_bytes": 128}) == 1
+    assert bench.effective_path(t(2), {"group_bytes": 512}) == 1
     assert bench.effective_path(t(1), {"group_bytes": 512}) == 1
     assert bench.effective_path(t(1), {"group_bytes": 1024}) == 0
     assert bench.effective_path(t(0), {"group_bytes": 16}) == 0
