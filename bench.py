@@ -236,12 +236,15 @@ def kernel_digest(kernel: str) -> str:
 _NCCL_DEVICE = None  # this rank's GPU when the process group is NCCL
 
 
-def dist_setup(backend: str):
+def dist_setup(backend: str, always: bool = False):
+    """Rank, local rank and world size from the launcher's environment; the
+    process group is started for more than one rank, or always when asked
+    (a one-rank group needs MASTER_ADDR and MASTER_PORT, as torchrun sets)."""
     global _NCCL_DEVICE
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 or always:
         import torch.distributed as dist
         if backend == "nccl":
             import torch
@@ -279,28 +282,43 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 
 
 def serving_section(idx, corpus, n_req: int, fracs=(0.1, 0.25, 0.5, 0.75, 0.9, 1.1), seed: int = 4):
+    """Poisson traces of n_req requests (log-normal lengths, median 300 bp,
+    70% from documents with 0.1% errors) at fractions of the plain batched
+    server's saturation rate, served by the continuous-batching engine and
+    by plain 256-request batches; every answer of the engine is checked
+    against the plain server's."""
     from paper_1910_04358_gb300 import serve, synth
     rng = np.random.default_rng([synth.GEN_SEED_BASE + 4, seed])
     _, lengths = synth.serving_trace(rng, n_req, rate_per_s=1.0)
-    # saturation: every request present at t = 0
     reqs0 = serve.make_requests(corpus, np.zeros(n_req), lengths, rng)
-    eng = serve.ServingEngine(idx, slots=4, max_batch_queries=1024, max_batch_bytes=2 << 20,
-                              mask_budget_bytes=max(64 << 20, 4 * 1024 * idx.W * 4))
-    eng.serve(reqs0[: min(n_req, 500)])  # warm
-    sat = eng.serve(reqs0).summary()
-    sat_rps = n_req / sat["wall_s"]
+    eng = serve.ServingEngine(idx, slots=4)
+    eng.serve(reqs0[: min(n_req, 2000)])  # warm
+    serve.plain_batched(idx, reqs0[: min(n_req, 2000)], batch_size=256)
+    # saturation: every request present at t = 0
+    plain_sat = serve.plain_batched(idx, reqs0, batch_size=256)
+    cont_sat = eng.serve(reqs0)
+    same = bool(np.array_equal(plain_sat.answers, cont_sat.answers))
+    ps, cs = plain_sat.summary(), cont_sat.summary()
+    sat_rps = n_req / ps["wall_s"]
     out = {"requests_per_rate": n_req, "length_dist": "log-normal median 300 bp, sigma 1, [31, 10^4]",
-           "saturation": {"requests_per_s": sat_rps, "bp_per_s": sat["bp_per_s"],
-                          "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]},
+           "rates_relative_to": "plain 256-request batches at saturation",
+           "saturation": {"plain_batch256": {"requests_per_s": sat_rps, "bp_per_s": ps["bp_per_s"],
+                                             "p50_ms": ps["p50_ms"], "p99_ms": ps["p99_ms"]},
+                          "continuous": {"requests_per_s": n_req / cs["wall_s"], "bp_per_s": cs["bp_per_s"],
+                                         "p50_ms": cs["p50_ms"], "p99_ms": cs["p99_ms"],
+                                         "batches": cs["batches"]}},
            "rates": []}
     for f in fracs:
         arrivals = np.cumsum(rng.exponential(1.0 / (f * sat_rps), size=n_req))
         reqs = [serve.Request(r.rid, r.packed, r.n_bases, float(a)) for r, a in zip(reqs0, arrivals)]
-        cont = eng.serve(reqs).summary()
-        plain = serve.plain_batched(idx, reqs, batch_size=256).summary()
+        cont = eng.serve(reqs)
+        plain = serve.plain_batched(idx, reqs, batch_size=256)
+        same = same and bool(np.array_equal(cont.answers, plain.answers))
+        c, pl = cont.summary(), plain.summary()
         out["rates"].append({"offered_frac_of_saturation": f, "offered_requests_per_s": f * sat_rps,
-                             "continuous": {k: cont[k] for k in ("p50_ms", "p99_ms", "bp_per_s", "batches", "max_in_flight")},
-                             "plain_batch256": {k: plain[k] for k in ("p50_ms", "p99_ms", "bp_per_s", "batches")}})
+                             "continuous": {k: c[k] for k in ("p50_ms", "p99_ms", "bp_per_s", "batches", "max_in_flight")},
+                             "plain_batch256": {k: pl[k] for k in ("p50_ms", "p99_ms", "bp_per_s", "batches")}})
+    out["answers_identical"] = same
     return out
 
 
@@ -559,6 +577,141 @@ def run_stream(args):
         print(json.dumps(line), flush=True)
     idx.close()
     return 0
+
+
+def run_sharded(args):
+    """--gpus N > 1: a document-sharded large index (Section 5.3).  Rank r
+    holds shard r, 10,000 documents of the large workload's recipe (shard 0
+    is the large corpus itself) as global documents r*10,000 .. r*10,000 +
+    9,999, and answers the same batch (the large workload's 10^5 sequences)
+    on it; one all_gather exchanges the shards' answers and every rank merges
+    them into the global answers (N*10,000 documents).  A step is that whole
+    pass.  Per-GPU work is one shard, fixed as N grows (weak scaling); the
+    units are k-mer queries against one shard, N per query k-mer."""
+    import torch
+    import torch.distributed as dist
+    rank, local, world = dist_setup("nccl", always=True)
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_1910_04358_gb300 import autotune, rambo, sharding, synth
+    t_start = time.time()
+    corpus0, q = synth.large_workload()
+    corpus = corpus0 if rank == 0 else synth.large_shard_corpus(rank)
+    del corpus0
+    p = corpus.params
+    n_seq_kmers, total_kmers, bp = batch_stats(p, np.zeros(0, np.uint64), q)
+    log(f"[bench] rank {rank}: shard generated in {time.time() - t_start:.1f} s")
+    osm = None
+    if rank == 0 and not args.no_oracle_check:
+        fk, fs = sample_fracs("large")
+        osm = OracleSample(p, np.zeros(0, np.uint64), q, fk, fs)
+        osm.start(corpus, max(1, (os.cpu_count() or 1) - 2))
+    to_dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
+    idx = rambo.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, device=local)
+    cached = autotune.load_cached(autotune.CACHE_FILE, autotune.cache_key(idx, q.n, total_kmers))
+    if cached:
+        idx.set_tuning(**cached)
+    idx.insert_batch_dev(to_dev(corpus.doc_ids, np.int32), to_dev(corpus.packed, np.uint8),
+                         to_dev(corpus.offsets, np.int64))
+    idx.sync()
+    K_all = world * p.K
+    member_lists = [np.arange(s * p.K, (s + 1) * p.K) for s in range(world)]
+    d_qp, d_qo = to_dev(q.packed, np.uint8), to_dev(q.offsets, np.int64)
+    local_out = torch.empty((q.n, idx.W), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        idx.query_batch_dev(None, d_qp, d_qo, out_seqs=local_out)
+        return sharding.gather_answers(local_out, member_lists, K_all)
+
+    for _ in range(args.warmup):
+        step()
+    idx.sync()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    idx.profile_reset(timed_stages=("probe_seqs",))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        glob = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(world)
+    idx.sync()
+    time.sleep(0.2)
+    clocks.stop()
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    prof = idx.profile_read()
+    launches = sum(v["launches"] for v in prof.values()) + args.steps * world  # + one merge kernel per shard
+    dom_ms = prof["probe_seqs"]["ms"] / max(prof["probe_seqs"]["timed"], 1)
+    info = idx.info
+    alg_bytes = probe_algorithmic_bytes(info, n_seq_kmers, q.n, q.n_bases)
+    if effective_path(idx.get_tuning(), info) == 1:
+        alg_bytes += q.n * idx.W * 4
+    peak, peak_src = measured_peak_gbs()
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    # the oracle check covers shard 0's documents, the first 10,000 global bits
+    oracle_check = None
+    if osm is not None:
+        first = glob[:, : (p.K + 31) // 32].clone()
+        if p.K % 32:
+            first[:, -1] &= (1 << (p.K % 32)) - 1
+        oracle_check = osm.check(None, first)
+    # end to end: page-locked inputs in, the global answers out on every rank
+    pin_p = torch.from_numpy(q.packed).pin_memory()
+    pin_o = torch.from_numpy(q.offsets.view(np.int64)).pin_memory()
+    pin_out = torch.empty(glob.shape, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def step_e2e():
+        d_qp.copy_(pin_p, non_blocking=True)
+        d_qo.copy_(pin_o, non_blocking=True)
+        g = step()
+        pin_out.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+
+    step_e2e()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_e2e()
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    value = world * total_kmers / (ms_step / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+        "config": {"workload": "large", "parallelism": f"document shards x{world}",
+                   "desc": (f"document-sharded large index: {world} shards of 10,000 docs x 500 kbp "
+                            "(R=5 B=100 m=2^29 eta=2 k=31, 32 GiB each), one per GPU, global documents "
+                            f"0..{K_all - 1}; batch = the large workload's 10^5 sequences of U[31,5000] bp "
+                            "sent to every shard; answers exchanged with one all_gather and merged"),
+                   "units": "k-mer queries against one shard (N per query k-mer)",
+                   "l2": "inputs larger than L2: index %.2f GB per GPU probed at random" % (info["index_bytes"] / 1e9)},
+        "query_bp_per_s": world * bp / (ms_step / 1e3), "kmers_per_step": world * total_kmers,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_fused_prep+k_fused (per rank)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": dom_ms,
+                     "peak_source": peak_src},
+        "clocks": clocks.summary(t_wall0, t_wall1),
+        "e2e": {"value": world * total_kmers / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(q.packed.nbytes + q.offsets.nbytes),
+                "d2h_bytes_per_step": int(glob.numel() * 4), "ms_per_step": 1e3 * t_e2e},
+        "cpu_baseline": None, "oracle_check": oracle_check,
+        "tuning": idx.get_tuning(), "tuning_source": "cached" if cached else "default",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.close()
+    dist.destroy_process_group()
+    return 0 if oracle_check is None or oracle_check["ok"] else 1
 
 
 def run_ours(args):
@@ -886,6 +1039,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["medium", "large", "tiny", "stream"], default="large")
+    ap.add_argument("--sharded", action="store_true",
+                    help="document-sharded run (the default for more than one rank; one rank needs torchrun)")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the CPU oracle check of the timed answers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -905,6 +1060,8 @@ def main():
         return run_reference(args)
     if args.workload == "stream":
         return run_stream(args)
+    if (int(os.environ.get("WORLD_SIZE", "1")) > 1 or args.sharded) and args.workload == "large":
+        return run_sharded(args)
     return run_ours(args)
 
 

@@ -179,6 +179,33 @@ int rambo_insert_batch_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
                            const uint64_t *base_offsets, void *workspace, size_t workspace_bytes,
                            void *stream);
 
+/* rambo_insert_batch_dev with documents given as separate ranges: document
+ * doc_ids[i] is bases [begins[i], ends[i]) of `packed` (n_docs entries each,
+ * device memory), so a subset of a packed corpus -- e.g. the documents one
+ * shard of a document-sharded index holds (Section 5.3) -- is inserted
+ * without repacking.  Ranges may overlap.  Workspace:
+ * rambo_insert_workspace(h, n_docs).  Same errors as rambo_insert_batch_dev;
+ * insert_mode 3 takes the direct insert here. */
+int rambo_insert_ranges_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                            const uint8_t *packed, uint64_t packed_bytes, const uint64_t *begins,
+                            const uint64_t *ends, void *workspace, size_t workspace_bytes,
+                            void *stream);
+
+/* Answers of a document-sharded deployment (Section 5.3: a routing hash
+ * sends each document to one shard, whose RAMBO holds it as a local
+ * document; the stacked structure answers a query with the union of the
+ * shards' answers, each placed at its documents' global ids).  ORs the n
+ * answer rows of one shard (shard_masks: n x shard_words uint32, bit j =
+ * local document j, j < shard_docs) into `out` (n x out_words uint32, bit d =
+ * global document d) at bits global_ids[j] (shard_docs uint32).  All
+ * pointers are device memory; `out` starts zeroed and is ORed into, so
+ * merging every shard yields the global answers.  Ids at or past
+ * 32*out_words are skipped.  Asynchronous on `stream`; RAMBO_EINVAL for
+ * missing pointers or shard_words < ceil(shard_docs/32). */
+int rambo_merge_shard_answers(uint64_t n, const uint32_t *shard_masks, uint32_t shard_words,
+                              uint32_t shard_docs, const uint32_t *global_ids, uint32_t *out,
+                              uint32_t out_words, void *stream);
+
 int rambo_query_kmers_dev(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out,
                           void *workspace, size_t workspace_bytes, void *stream);
 
@@ -214,9 +241,13 @@ int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, u
  * RAMBO_STATIC_SCRATCH_BYTES is rejected with RAMBO_EINVAL before anything is
  * enqueued.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, once per device); make that first call before any
- * stream capture.  Every call on a device shares the one array, so calls
- * whose work can overlap on the GPU (different streams, or handles on the
- * same device) race: serialise them. */
+ * stream capture.  The address is kept for the rest of the process, so
+ * after a cudaDeviceReset of that device (which ends every handle on it as
+ * well) this entry point must not be called again in the same process.
+ * Every call on a device shares the one array, so calls whose work can
+ * overlap on the GPU (different streams, or handles on the same device)
+ * race: serialise them.  With query_path 2 the region-binned path runs when
+ * its record bins fit the array as well, else path 1. */
 #define RAMBO_STATIC_SCRATCH_BYTES (8u << 20)
 int rambo_query_seqs_noalloc(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
                              const uint64_t *base_offsets, uint32_t *out, void *stream);

@@ -86,6 +86,7 @@ def _load():
             "orc_insert_words": (C.c_int, [p, u32, p, p, u64]),
             "orc_query_words": (C.c_int, [p, p, p, u64, p]),
             "orc_seq_positions": (C.c_int, [p, u64, p, p, p]),
+            "orc_position_bits": (C.c_int, [p, u64, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -293,6 +294,16 @@ class Rambo:
         out = np.zeros((nbits + 63) // 64, dtype=np.uint64)
         _load().orc_filter_words(self._h, r, b, _ptr(out))
         return out
+
+    def position_bits(self, positions) -> np.ndarray:
+        """Bits of all R*B BFUs at each position: row i holds bit r*B + b
+        (LSB-first bytes, ceil(R*B/8) of them) = filter (r,b) at positions[i]."""
+        pos = np.ascontiguousarray(positions, dtype=np.uint64)
+        row = (self.R * self.B + 7) // 8
+        out = np.zeros((max(pos.size, 1), row), dtype=np.uint8)
+        if pos.size:
+            _check(_load().orc_position_bits(self._h, pos.size, _ptr(pos), _ptr(out)), "position_bits")
+        return out[:pos.size]
 
     def fill_fraction(self, r: int, b: int) -> float:
         nbits = int(_load().orc_num_filters_bits(self._h))

@@ -666,3 +666,18 @@ uint64_t orc_filter_popcount(const orc_rambo *o, uint32_t r, uint32_t b) {
     return c;
 }
 int orc_is_inserted(const orc_rambo *o, uint32_t d) { return o->inserted[d]; }
+/* The bits of every BFU at each of n positions: for position i, bit
+ * r*B + b of the R*B-bit string at out + i * ceil(R*B/8) (LSB-first within
+ * a byte) is bit pos[i] of filter (r,b).  ORC_EUNTRACKED if a position is
+ * not kept (restricted mode). */
+int orc_position_bits(const orc_rambo *o, uint64_t n, const uint64_t *pos, uint8_t *out) {
+    const uint64_t nbf = (uint64_t)o->R * o->B, row = (nbf + 7) / 8;
+    memset(out, 0, n * row);
+    for (uint64_t i = 0; i < n; ++i) {
+        const int64_t s = orc_slot(o, pos[i]);
+        if (s < 0) return ORC_EUNTRACKED;
+        for (uint64_t f = 0; f < nbf; ++f)
+            if (orc_get_bit(o->filter[f], (uint64_t)s)) out[i * row + f / 8] |= (uint8_t)(1u << (f % 8));
+    }
+    return ORC_OK;
+}

@@ -501,8 +501,13 @@ int query_kmers_enqueue(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t 
     return RAMBO_OK;
 }
 
+// Documents are [begins[i], ends[i]); a CSR batch passes (offsets, offsets +
+// 1).  Ranges that are not a CSR batch may overlap, so the region-binned
+// insert (whose chunks assume at most one k-mer per packed base) is not used
+// for them.
 int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_t *packed,
-                   uint64_t packed_bytes, const uint64_t *offsets, void *ws, cudaStream_t s) {
+                   uint64_t packed_bytes, const uint64_t *offsets, const uint64_t *ends, void *ws,
+                   cudaStream_t s) {
     const Geometry &g = h->g;
     h->any_inserted = true;
     const InsWs L = ins_ws(n);
@@ -516,7 +521,7 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     }
     {
         StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
-        RAMBO_TRY(launch_kmer_prefix(offsets, offsets + 1, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
+        RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
     }
     InsertArgs a{};
     a.index = h->d_index;
@@ -541,7 +546,7 @@ int insert_enqueue(rambo_t *h, uint64_t n, const uint32_t *doc_ids, const uint8_
     a.mode = h->tune.insert_mode;
     uint32_t rshift = 0;
     uint32_t nbins =
-        a.mode == 3 && h->d_bins
+        a.mode == 3 && h->d_bins && ends == offsets + 1
             ? binned_insert_bins(g.m, g.Gw * 4, g.K,
                                  (uint64_t)(h->tune.bin_region_kib ? h->tune.bin_region_kib : 32768) * 1024,
                                  &rshift)
@@ -955,8 +960,33 @@ int rambo_insert_batch_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
         return RAMBO_EINVAL;
     DeviceGuard guard(h->device);
     if (!guard.ok) return RAMBO_ECUDA;
-    return insert_enqueue(h, n_docs, doc_ids, packed, packed_bytes, base_offsets, workspace,
+    return insert_enqueue(h, n_docs, doc_ids, packed, packed_bytes, base_offsets, base_offsets + 1, workspace,
                           static_cast<cudaStream_t>(stream));
+}
+
+int rambo_insert_ranges_dev(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
+                            const uint8_t *packed, uint64_t packed_bytes, const uint64_t *begins,
+                            const uint64_t *ends, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (n_docs == 0) return RAMBO_OK;
+    if (!doc_ids || !begins || !ends || !workspace || (!packed && packed_bytes) ||
+        workspace_bytes < ins_ws(n_docs).total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return RAMBO_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return RAMBO_ECUDA;
+    return insert_enqueue(h, n_docs, doc_ids, packed, packed_bytes, begins, ends, workspace,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int rambo_merge_shard_answers(uint64_t n, const uint32_t *shard_masks, uint32_t shard_words,
+                              uint32_t shard_docs, const uint32_t *global_ids, uint32_t *out,
+                              uint32_t out_words, void *stream) {
+    if (n == 0 || shard_docs == 0) return RAMBO_OK;
+    if (!shard_masks || !global_ids || !out || shard_words < (shard_docs + 31) / 32 || out_words == 0)
+        return RAMBO_EINVAL;
+    return cuda_rc(launch_merge_shard(n, shard_masks, shard_words, shard_docs, global_ids, out, out_words,
+                                      static_cast<cudaStream_t>(stream)));
 }
 
 int rambo_query_kmers_dev(rambo_t *h, uint64_t n, const uint64_t *kmers, uint32_t *out,
@@ -1082,7 +1112,7 @@ int rambo_insert_batch(rambo_t *h, uint32_t n_docs, const uint32_t *doc_ids,
     if (rc) return rc;
     uint32_t *d_ids = reinterpret_cast<uint32_t *>(st.rest);
     RAMBO_TRY(cudaMemcpyAsync(d_ids, doc_ids, (size_t)n_docs * 4, cudaMemcpyHostToDevice, h->stream));
-    rc = insert_enqueue(h, n_docs, d_ids, st.packed, st.packed_bytes + 16, st.offsets,
+    rc = insert_enqueue(h, n_docs, d_ids, st.packed, st.packed_bytes + 16, st.offsets, st.offsets + 1,
                         st.rest + ids_sz, h->stream);
     if (rc) return rc;
     RAMBO_TRY(cudaStreamSynchronize(h->stream));

@@ -267,6 +267,12 @@ cudaError_t launch_register_docs(const uint32_t *doc_ids, uint64_t n, const uint
                                  uint32_t K, uint32_t R, uint32_t B, uint32_t W, uint32_t *docbits,
                                  uint32_t *err, cudaStream_t s);
 cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s);
+// ORs the answers of one document shard (n rows of shard_words words, bit j
+// = the shard's local document j) into global answer rows of out_words
+// words at bit global_ids[j] (device array of shard_docs ids).
+cudaError_t launch_merge_shard(uint64_t n, const uint32_t *shard_masks, uint32_t shard_words,
+                               uint32_t shard_docs, const uint32_t *global_ids, uint32_t *out,
+                               uint32_t out_words, cudaStream_t s);
 // Folding over B -> B/2 of the index (groups up to 512 bytes) and DocBits.
 cudaError_t launch_fold(const uint32_t *old_index, uint32_t old_gw, uint32_t *new_index,
                         uint32_t new_gw, uint64_t m, uint32_t B, uint32_t R,

@@ -427,6 +427,40 @@ cudaError_t launch_insert(const InsertArgs &a, int sm_count, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// Document-sharded answers (Section 5.3): shard s holds the documents that
+// the routing hash sends to it, as local documents 0..K_s-1; the global
+// answer of a query is the union over shards of their answers placed at the
+// documents' global ids (the shards' documents are disjoint, so this is a
+// concatenation in global document order).  One thread per (query, shard
+// word): each set bit is ORed into the global row.
+namespace {
+__global__ void k_merge_shard(uint64_t n, const uint32_t *masks, uint32_t sw, uint32_t sd,
+                              const uint32_t *gid, uint32_t *out, uint32_t ow) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * sw) return;
+    const uint64_t q = i / sw;
+    const uint32_t w = (uint32_t)(i - q * sw);
+    uint32_t v = masks[i];
+    while (v) {
+        const uint32_t j = 32 * w + (uint32_t)(__ffs(v) - 1);
+        v &= v - 1;
+        if (j >= sd) break;
+        const uint32_t d = gid[j];
+        if (d / 32 < ow) atomicOr(out + q * ow + d / 32, 1u << (d & 31));
+    }
+}
+}  // namespace
+
+cudaError_t launch_merge_shard(uint64_t n, const uint32_t *shard_masks, uint32_t shard_words,
+                               uint32_t shard_docs, const uint32_t *global_ids, uint32_t *out,
+                               uint32_t out_words, cudaStream_t s) {
+    const uint64_t items = n * shard_words;
+    k_merge_shard<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(n, shard_masks, shard_words, shard_docs,
+                                                                   global_ids, out, out_words);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Failure-detection check of a bounded device wait: one thread polls an
 // mbarrier that nothing ever completes (no arrivals are made), without
 // suspending, and gives up after `spins` polls by latching ERR_WAIT.  Nothing

@@ -30,7 +30,9 @@ std::mutex g_mutex;
 void *g_scratch_on_device[kMaxDevices];  // device address of g_scratch, per device
 
 // Looks up (once per device, with that device current) the device address of
-// the scratch array.
+// the scratch array.  The address is kept until the process exits; a
+// cudaDeviceReset of the device would make it stale, which is why the entry
+// point must not be used after one (the header says so).
 int scratch_address(int device, void **out) {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch_on_device[device]) {

@@ -65,6 +65,8 @@ def load():
             "rambo_query_seqs_workspace": (sz, [p, u64]),
             "rambo_insert_batch_dev": (i, [p, u32, p, p, u64, p, p, sz, p]),
             "rambo_query_kmers_dev": (i, [p, u64, p, p, p, sz, p]),
+            "rambo_insert_ranges_dev": (i, [p, u32, p, p, u64, p, p, p, sz, p]),
+            "rambo_merge_shard_answers": (i, [u64, p, u32, u32, p, p, u32, p]),
             "rambo_query_seqs_dev": (i, [p, u64, p, u64, p, p, p, sz, p]),
             "rambo_sync": (i, [p, p]),
             "rambo_copy_index": (i, [p, u64, u64, p]),
@@ -307,6 +309,17 @@ class Index:
                                              packed.numel(), _t_ptr(offsets), wp, wn, s),
                "rambo_insert_batch_dev")
 
+    def insert_ranges_dev(self, doc_ids, packed, begins, ends, stream=None, workspace=None):
+        """Documents doc_ids[i] = bases [begins[i], ends[i]) of `packed` (int32/
+        uint32, uint8, int64, int64 CUDA tensors)."""
+        n = doc_ids.numel()
+        need = self.workspace_bytes("insert", n)
+        s = _stream_handle(stream)
+        wp, wn = workspace if workspace is not None else self._workspace(s, need)
+        _check(load().rambo_insert_ranges_dev(self._h, n, _t_ptr(doc_ids), _t_ptr(packed),
+                                              packed.numel(), _t_ptr(begins), _t_ptr(ends), wp, wn, s),
+               "rambo_insert_ranges_dev")
+
     def query_kmers_dev(self, kmers, out=None, stream=None, workspace=None):
         """kmers int64 CUDA tensor of forward codes; returns (n, W) int32 masks."""
         import torch
@@ -488,6 +501,18 @@ class Index:
         out = np.zeros((self.K, self.R), dtype=np.uint32)
         _check(load().rambo_copy_partition(self._h, _np_ptr(out)), "rambo_copy_partition")
         return out
+
+
+def merge_shard_answers(shard_masks, global_ids, out, stream=None):
+    """ORs one document shard's answers (n x Ws int32 CUDA tensor, bit j =
+    local document j) into the global answers `out` (n x W int32 CUDA
+    tensor) at bits global_ids[j] (int32 CUDA tensor of the shard's
+    documents' global ids)."""
+    n, ws = shard_masks.shape
+    _check(load().rambo_merge_shard_answers(n, _t_ptr(shard_masks), ws, global_ids.numel(),
+                                            _t_ptr(global_ids), _t_ptr(out), out.shape[1],
+                                            _stream_handle(stream)), "rambo_merge_shard_answers")
+    return out
 
 
 def answer_docs(mask_row) -> np.ndarray:

@@ -2,24 +2,30 @@
 
 Requests (2-bit packed sequences) arrive over time.  The engine keeps the
 index resident in HBM and a fixed set of slots, each with its own CUDA stream,
-pinned host buffers, device buffers and query workspace.  Whenever a slot is
-free it forms the next batch from the requests that have arrived, in arrival
-order, bounded by the slot's capacity and by an output-mask memory budget
-(the answers of all batches in flight must fit it), copies the batch in,
-enqueues the query and the copy of the answers back on the slot's stream,
-and moves on: batches on different slots overlap on the device.  Each
-request is packed at a byte boundary of the slot buffer and passed as a
-[begin, end) range, so no bases are shifted on the host.
+page-locked host buffers, device buffers and query workspace.  Whenever a
+slot is free it forms the next batch from the requests that have arrived, in
+arrival order, bounded by the slot's capacity (queries and bytes) and by an
+output-mask memory budget (the answers of all batches in flight must fit it),
+copies the batch in, enqueues the query and the copy of the answers back on
+the slot's stream, and moves on: batches on different slots overlap on the
+device.
+
+Arriving requests are kept in one page-locked arena, each packed at a byte
+boundary, in arrival order, so the requests of a batch are one contiguous
+span of it: a batch costs one host-to-device copy of its bytes, its
+[begin, end) ranges are computed for all of its requests at once, and its
+answers are copied from the device straight into their rows of a
+page-locked answer array kept in the same order.
 
 `plain_batched` serves the same trace the simple way for comparison: wait
-for a fixed number of arrivals, run one synchronous batch, repeat.
+for a fixed number of arrivals, run one batch through the device API, wait
+for it, repeat.
 
 Both return per-request answers (bit-identical to querying each request
 alone) and latencies (completion time - arrival time).
 """
 from __future__ import annotations
 
-import collections
 import time
 from dataclasses import dataclass, field
 
@@ -37,7 +43,7 @@ class Request:
 @dataclass
 class ServeResult:
     latency_s: np.ndarray
-    answers: list
+    answers: np.ndarray    # (requests, W) uint32, by request id
     wall_s: float
     bases: int
     batches: int
@@ -53,31 +59,90 @@ class ServeResult:
                 "max_in_flight": self.max_in_flight, **self.stats}
 
 
+class _Trace:
+    """A request trace in arrival order, its bytes in one page-locked arena."""
+
+    def __init__(self, requests: list[Request], max_bytes: int):
+        import torch
+        n = len(requests)
+        if sorted(r.rid for r in requests) != list(range(n)):
+            raise ValueError("request ids must be 0 .. len(requests) - 1")
+        big = [r.rid for r in requests if r.packed.size > max_bytes]
+        if big:
+            raise ValueError(f"requests {big[:5]} exceed the batch byte limit of {max_bytes}")
+        arr = np.array([r.arrival for r in requests], dtype=np.float64)
+        self.order = np.argsort(arr, kind="stable")
+        self.arrival = arr[self.order]
+        self.rid = np.array([requests[i].rid for i in self.order], dtype=np.int64)
+        sizes = np.array([requests[i].packed.size for i in self.order], dtype=np.int64)
+        self.n_bases = np.array([requests[i].n_bases for i in self.order], dtype=np.int64)
+        self.bstart = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(sizes, out=self.bstart[1:])
+        self.arena = torch.empty(int(self.bstart[-1]) + 16, dtype=torch.uint8, pin_memory=True)
+        if n:
+            self.arena.numpy()[: self.bstart[-1]] = np.concatenate([requests[i].packed for i in self.order])
+        self.n = n
+        self.bases = int(self.n_bases.sum())
+        self.answers = None  # page-locked answers in arrival order (set by the server)
+
+    def answer_buffer(self, W: int):
+        """Page-locked (n, W) answers in arrival order: each batch's answers
+        are copied from the device straight into their rows."""
+        import torch
+        self.answers = torch.empty((max(self.n, 1), W), dtype=torch.int32, pin_memory=True)
+        return self.answers
+
+    def by_request(self) -> np.ndarray:
+        """The answers indexed by request id."""
+        out = np.empty((self.n, self.answers.shape[1]), dtype=np.uint32)
+        out[self.rid] = self.answers.numpy()[: self.n].view(np.uint32)
+        return out
+
+    def ranges(self, i0: int, i1: int, begins: np.ndarray, ends: np.ndarray):
+        """[begin, end) in bases of requests i0..i1 within their span."""
+        b = 4 * (self.bstart[i0:i1] - self.bstart[i0])
+        begins[: i1 - i0] = b
+        ends[: i1 - i0] = b + self.n_bases[i0:i1]
+
+
 class _Slot:
     def __init__(self, idx, max_queries: int, max_bytes: int, device):
         import torch
         self.stream = torch.cuda.Stream(device=device)
-        self.h_packed = torch.empty(max_bytes + 16, dtype=torch.uint8, pin_memory=True)
         self.h_begin = torch.empty(max_queries, dtype=torch.int64, pin_memory=True)
         self.h_end = torch.empty(max_queries, dtype=torch.int64, pin_memory=True)
-        self.h_out = torch.empty((max_queries, idx.W), dtype=torch.int32, pin_memory=True)
         self.d_packed = torch.empty(max_bytes + 16, dtype=torch.uint8, device=device)
         self.d_begin = torch.empty(max_queries, dtype=torch.int64, device=device)
         self.d_end = torch.empty(max_queries, dtype=torch.int64, device=device)
         self.d_out = torch.empty((max_queries, idx.W), dtype=torch.int32, device=device)
-        ws_bytes = idx.workspace_bytes("seqs", max_queries)
+        ws_bytes = idx.workspace_bytes("seqs", max_queries, max_bytes)
         self.ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=device)
         base = self.ws.data_ptr()
         self.ws_ptr = ((base + 255) // 256 * 256, ws_bytes)
         self.event = torch.cuda.Event()
-        self.batch: list[Request] = []
+        self.span = (0, 0)     # requests [i0, i1) of the trace in this slot
         self.busy = False
-        self.mask_bytes = 0
+
+    def launch(self, idx, tr: _Trace, i0: int, i1: int):
+        import torch
+        n = i1 - i0
+        b0, b1 = int(tr.bstart[i0]), int(tr.bstart[i1])
+        tr.ranges(i0, i1, self.h_begin.numpy(), self.h_end.numpy())
+        with torch.cuda.stream(self.stream):
+            self.d_packed[: b1 - b0].copy_(tr.arena[b0:b1], non_blocking=True)
+            self.d_begin[:n].copy_(self.h_begin[:n], non_blocking=True)
+            self.d_end[:n].copy_(self.h_end[:n], non_blocking=True)
+            idx.query_ranges_dev(self.d_packed[: b1 - b0], self.d_begin[:n], self.d_end[:n],
+                                 out=self.d_out[:n], stream=self.stream, workspace=self.ws_ptr)
+            tr.answers[i0:i1].copy_(self.d_out[:n], non_blocking=True)
+            self.event.record(self.stream)
+        self.span = (i0, i1)
+        self.busy = True
 
 
 class ServingEngine:
-    def __init__(self, idx, slots: int = 4, max_batch_queries: int = 2048,
-                 max_batch_bytes: int = 4 << 20, mask_budget_bytes: int = 64 << 20,
+    def __init__(self, idx, slots: int = 4, max_batch_queries: int = 8192,
+                 max_batch_bytes: int = 8 << 20, mask_budget_bytes: int = 256 << 20,
                  device: int | None = None):
         import torch
         self.idx = idx
@@ -88,132 +153,98 @@ class ServingEngine:
         self.slots = [_Slot(idx, max_batch_queries, max_batch_bytes, self.device)
                       for _ in range(slots)]
 
-    # -- one batch ---------------------------------------------------------
-    def _launch(self, slot: _Slot, batch: list[Request]):
-        import torch
-        W = self.idx.W
-        pos = 0
-        hp = slot.h_packed.numpy()
-        hb, he = slot.h_begin.numpy(), slot.h_end.numpy()
-        for i, r in enumerate(batch):
-            nb = r.packed.size
-            hp[pos:pos + nb] = r.packed
-            hb[i] = 4 * pos
-            he[i] = 4 * pos + r.n_bases
-            pos += nb
-        n = len(batch)
-        with torch.cuda.stream(slot.stream):
-            slot.d_packed[:pos].copy_(slot.h_packed[:pos], non_blocking=True)
-            slot.d_begin[:n].copy_(slot.h_begin[:n], non_blocking=True)
-            slot.d_end[:n].copy_(slot.h_end[:n], non_blocking=True)
-            self.idx.query_ranges_dev(slot.d_packed[:pos], slot.d_begin[:n], slot.d_end[:n],
-                                      out=slot.d_out[:n], stream=slot.stream,
-                                      workspace=slot.ws_ptr)
-            slot.h_out[:n].copy_(slot.d_out[:n], non_blocking=True)
-            slot.event.record(slot.stream)
-        slot.batch = batch
-        slot.busy = True
-        slot.mask_bytes = n * W * 4
-
-    def _collect(self, slot: _Slot, now: float, answers: list, done_at: np.ndarray):
-        out = slot.h_out.numpy()
-        for i, r in enumerate(slot.batch):
-            answers[r.rid] = out[i].view(np.uint32).copy()
-            done_at[r.rid] = now
-        slot.busy = False
-        slot.batch = []
-        released = slot.mask_bytes
-        slot.mask_bytes = 0
-        return released
+    def _batch_end(self, tr: _Trace, head: int, avail: int, in_flight_mask: int) -> int:
+        """Last request (exclusive) of the next batch from the arrived
+        requests [head, avail): at least one, then as many as the query and
+        byte limits and the output-mask budget allow."""
+        row = self.idx.W * 4
+        by_mask = (self.mask_budget - in_flight_mask) // row
+        cap = max(1, min(self.max_q, by_mask))
+        end = min(avail, head + cap)
+        by_bytes = int(np.searchsorted(tr.bstart, tr.bstart[head] + self.max_bytes, side="right")) - 1
+        return max(head + 1, min(end, by_bytes))
 
     # -- continuous batching ----------------------------------------------
     def serve(self, requests: list[Request], spin_sleep: float = 20e-6) -> ServeResult:
-        n = len(requests)
-        order = sorted(range(n), key=lambda i: requests[i].arrival)
-        answers = [None] * n
+        tr = _Trace(requests, self.max_bytes)
+        tr.answer_buffer(self.idx.W)
+        n = tr.n
         done_at = np.zeros(n)
-        pending = collections.deque()
-        nxt = 0
+        head = 0            # first request not yet in a batch (arrival order)
+        finished = 0
         in_flight_mask = 0
         batches = 0
         max_in_flight = 0
-        W4 = self.idx.W * 4
+        row = self.idx.W * 4
         t0 = time.perf_counter()
-        finished = 0
         while finished < n:
             now = time.perf_counter() - t0
-            while nxt < n and requests[order[nxt]].arrival <= now:
-                pending.append(requests[order[nxt]])
-                nxt += 1
             for sl in self.slots:
                 if sl.busy and sl.event.query():
-                    in_flight_mask -= self._collect(sl, time.perf_counter() - t0, answers, done_at)
-                    finished += 0  # counted below
-            finished = sum(1 for a in answers if a is not None)
+                    i0, i1 = sl.span
+                    done_at[tr.rid[i0:i1]] = time.perf_counter() - t0
+                    finished += i1 - i0
+                    in_flight_mask -= (i1 - i0) * row
+                    sl.busy = False
+            avail = int(np.searchsorted(tr.arrival, now, side="right"))
             launched = False
             for sl in self.slots:
-                if not pending:
+                if head >= avail:
                     break
                 if sl.busy:
                     continue
-                batch, nbytes = [], 0
-                while pending and len(batch) < self.max_q:
-                    r = pending[0]
-                    if nbytes + r.packed.size > self.max_bytes and batch:
-                        break
-                    if in_flight_mask + (len(batch) + 1) * W4 > self.mask_budget and batch:
-                        break
-                    batch.append(pending.popleft())
-                    nbytes += r.packed.size
-                if not batch:
+                if in_flight_mask + row > self.mask_budget and any(s.busy for s in self.slots):
                     break
-                self._launch(sl, batch)
-                in_flight_mask += len(batch) * W4
+                end = self._batch_end(tr, head, avail, in_flight_mask)
+                sl.launch(self.idx, tr, head, end)
+                in_flight_mask += (end - head) * row
+                head = end
                 batches += 1
                 launched = True
             max_in_flight = max(max_in_flight, sum(1 for sl in self.slots if sl.busy))
             if not launched:
-                if nxt < n and not pending and not any(sl.busy for sl in self.slots):
-                    wait = requests[order[nxt]].arrival - (time.perf_counter() - t0)
+                if head < n and head >= avail and not any(sl.busy for sl in self.slots):
+                    wait = tr.arrival[head] - (time.perf_counter() - t0)
                     if wait > 0:
                         time.sleep(min(wait, 1e-3))
                 else:
                     time.sleep(spin_sleep)
         wall = time.perf_counter() - t0
-        lat = np.array([done_at[i] - requests[i].arrival for i in range(n)])
-        bases = sum(r.n_bases for r in requests)
-        return ServeResult(lat, answers, wall, bases, batches, max_in_flight,
+        lat = done_at - np.array([r.arrival for r in sorted(requests, key=lambda r: r.rid)])
+        return ServeResult(lat, tr.by_request(), wall, tr.bases, batches, max_in_flight,
                            {"mode": "continuous", "slots": len(self.slots)})
 
 
-def plain_batched(idx, requests: list[Request], batch_size: int) -> ServeResult:
+def plain_batched(idx, requests: list[Request], batch_size: int, max_batch_bytes: int = 8 << 20) -> ServeResult:
     """Fixed-size batches, one at a time: wait for batch_size arrivals (or the
-    end of the trace), query synchronously through the host-buffer ABI."""
-    from .synth import PackedStream, unpack_bases
-    n = len(requests)
-    order = sorted(range(n), key=lambda i: requests[i].arrival)
-    answers = [None] * n
+    end of the trace), run the batch through the device API with page-locked
+    buffers (bytes in, ranges in, query, answers out) and wait for it."""
+    import torch
+    tr = _Trace(requests, max_batch_bytes)
+    tr.answer_buffer(idx.W)
+    n = tr.n
+    dev = torch.device(f"cuda:{idx.device}")
+    sl = _Slot(idx, batch_size, max(max_batch_bytes, 16), dev)
     done_at = np.zeros(n)
     t0 = time.perf_counter()
     batches = 0
-    for s in range(0, n, batch_size):
-        group = [requests[i] for i in order[s:s + batch_size]]
-        last_arrival = group[-1].arrival
+    i0 = 0
+    while i0 < n:
+        i1 = min(n, i0 + batch_size)
+        # the batch's bytes must fit the slot
+        i1 = max(i0 + 1, min(i1, int(np.searchsorted(tr.bstart, tr.bstart[i0] + max_batch_bytes,
+                                                            side="right")) - 1))
+        last_arrival = tr.arrival[i1 - 1]
         while time.perf_counter() - t0 < last_arrival:
             time.sleep(min(1e-3, max(0.0, last_arrival - (time.perf_counter() - t0))))
-        ps = PackedStream()
-        for r in group:
-            ps.append(unpack_bases(r.packed, 0, r.n_bases))
-        packed, offs = ps.finish()
-        out = idx.query_seqs(packed, offs)
-        now = time.perf_counter() - t0
-        for i, r in enumerate(group):
-            answers[r.rid] = out[i]
-            done_at[r.rid] = now
+        sl.launch(idx, tr, i0, i1)
+        sl.stream.synchronize()
+        done_at[tr.rid[i0:i1]] = time.perf_counter() - t0
         batches += 1
+        i0 = i1
     wall = time.perf_counter() - t0
-    lat = np.array([done_at[i] - requests[i].arrival for i in range(n)])
-    return ServeResult(lat, answers, wall, sum(r.n_bases for r in requests), batches, 1,
+    lat = done_at - np.array([r.arrival for r in sorted(requests, key=lambda r: r.rid)])
+    return ServeResult(lat, tr.by_request(), wall, tr.bases, batches, 1,
                        {"mode": "plain", "batch_size": batch_size})
 
 

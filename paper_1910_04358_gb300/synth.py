@@ -302,6 +302,18 @@ def large_workload(n_docs: int | None = None, doc_len: int = 500_000, n_queries:
     return corpus, q
 
 
+def large_shard_corpus(shard: int, n_docs: int | None = None, doc_len: int = 500_000) -> Corpus:
+    """The documents of shard `shard` of a document-sharded large index
+    (Section 5.3): shard 0 is the large workload's own corpus; shard s > 0
+    draws another 10,000 documents from the same recipe with its own seed."""
+    if shard == 0:
+        return large_workload(n_docs=n_docs, doc_len=doc_len, n_queries=0)[0]
+    p = WORKLOAD_PARAMS[LARGE]
+    if n_docs is not None:
+        p = Params(K=n_docs, B=p.B, R=p.R, m=p.m, eta=p.eta)
+    return family_corpus(rng_for(LARGE, 1000 + shard), p, 200, doc_len, 0.005, 0.0005)
+
+
 def serving_trace(rng, n: int, rate_per_s: float, median: float = 300.0, sigma: float = 1.0,
                   lo: int = 31, hi: int = 10_000):
     """Poisson arrivals (seconds) and log-normal query lengths clipped to [lo, hi]."""

@@ -697,3 +697,54 @@ def test_word_documents_match_oracle(rambo_lib):
     got = idx.query_words(queries)
     want = np.stack([o.query_words(q) for q in queries])
     assert np.array_equal(got, want)
+
+
+# ------------------------------------- document shards: range inserts, merge
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_insert_ranges_subset_and_overlap_match_oracle(rambo_lib, mode):
+    # a shard inserts some of a corpus's documents straight from the shared
+    # packed stream: out of order, one twice (idempotent), and a range that
+    # overlaps another (insert_mode 3 takes the direct insert for ranges)
+    torch = _torch()
+    p = synth.Params(K=60, B=16, R=3, m=1 << 14, eta=2, k=31, seed=12)
+    rng = np.random.default_rng(7)
+    corpus = synth.family_corpus(rng, p, n_seeds=8, doc_len=700, sub_rate=0.02)
+    offs = corpus.offsets.astype(np.int64)
+    pick = np.array([40, 3, 17, 3, 59, 22], dtype=np.int64)
+    begins, ends = offs[pick].copy(), offs[pick + 1].copy()
+    begins[-1] = offs[17] + 100  # doc 22's slot reads part of doc 17 instead
+    ends[-1] = offs[18] + 50
+    idx = rambo_lib.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    idx.set_tuning(insert_mode=mode)
+    idx.insert_ranges_dev(_dev(pick.astype(np.int32), np.int32), _dev(corpus.packed, np.uint8),
+                          _dev(begins, np.int64), _dev(ends, np.int64))
+    idx.sync()
+    o = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    for d, b0, b1 in zip(pick.tolist(), begins.tolist(), ends.tolist()):
+        o.insert(d, corpus.packed, b0, b1 - b0)
+    assert_index_equal(idx, o, p)
+    assert_docbits_equal(idx, o, p)
+    q = synth.sample_queries(rng, corpus, rng.integers(25, 300, size=120), 0.7)
+    assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), o.query_seqs(q.packed, q.offsets))
+
+
+def test_merge_shard_answers_places_bits_at_global_ids(rambo_lib):
+    torch = _torch()
+    from paper_1910_04358_gb300 import sharding
+    rng = np.random.default_rng(3)
+    K, n, S = 1000, 300, 3
+    tau = sharding.route(K, S, seed=5)
+    mem = sharding.members(tau, S)
+    parts, out = [], torch.zeros((n, (K + 31) // 32), dtype=torch.int32, device="cuda")
+    for s in range(S):
+        ws = (mem[s].size + 31) // 32 + 1  # a padded shard row
+        local = rng.integers(0, 1 << 32, size=(n, ws), dtype=np.uint64).astype(np.uint32)
+        local[:, (mem[s].size + 31) // 32:] = 0
+        if mem[s].size % 32:
+            local[:, mem[s].size // 32] &= np.uint32((1 << (mem[s].size % 32)) - 1)
+        parts.append((local, mem[s]))
+        rambo_lib.merge_shard_answers(_dev(local.view(np.int32), np.int32).view(n, ws),
+                                      _dev(mem[s].astype(np.int32), np.int32), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(rambo_lib.as_u32(out), sharding.merge_answers_host(n, K, parts))

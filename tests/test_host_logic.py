@@ -117,3 +117,14 @@ def test_autotune_revisits_a_knob_once_a_later_one_moves(monkeypatch):
     res = autotune.autotune(idx, lambda: None, lambda: [out], reps=1)
     assert res["best"]["fused_async"] == 1 and res["best"]["expand_ctas_per_sm"] == 2
     assert abs(res["ms"] - 0.90) < 1e-9
+
+
+def test_serving_trace_refuses_requests_beyond_the_batch_bytes():
+    import pytest
+    from paper_1910_04358_gb300 import serve
+    small = serve.Request(0, np.zeros(100, np.uint8), 400, 0.0)
+    big = serve.Request(1, np.zeros(5000, np.uint8), 20000, 0.0)
+    with pytest.raises(ValueError):
+        serve._Trace([small, big], max_bytes=4096)
+    with pytest.raises(ValueError):  # ids must be 0 .. n-1
+        serve._Trace([serve.Request(3, np.zeros(4, np.uint8), 16, 0.0)], max_bytes=4096)

@@ -392,6 +392,27 @@ def test_bulk_positions_match_string_brute_force_and_tracking_oracle_is_exact():
     assert np.array_equal(t.query_kmers(kmers), full.query_kmers(kmers))
 
 
+def test_position_bits_match_per_filter_bits():
+    p, corpus, q = _small_case(K=40, B=5, R=3, m=1 << 13)
+    o = _build(p, corpus)
+    rng = np.random.default_rng(9)
+    pos = rng.integers(0, p.m, size=200).astype(np.uint64)
+    got = o.position_bits(pos)
+    assert got.shape == (200, (p.R * p.B + 7) // 8)
+    for i, x in enumerate(pos.tolist()):
+        for r in range(p.R):
+            for b in range(p.B):
+                f = r * p.B + b
+                assert (got[i, f // 8] >> (f % 8)) & 1 == o.filter_bit(r, b, x)
+    # restricted mode: tracked positions agree, an untracked one is refused
+    t = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed, tracked=pos[:50])
+    t.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
+    assert np.array_equal(t.position_bits(pos[:50]), got[:50])
+    untracked = int(np.setdiff1d(np.arange(p.m, dtype=np.uint64), pos[:50])[0])
+    with pytest.raises(oracle.OracleError):
+        t.position_bits([untracked])
+
+
 def test_invalid_arguments():
     with pytest.raises(oracle.OracleError):
         oracle.Rambo(0, 1, 1, 8, 1)

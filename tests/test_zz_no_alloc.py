@@ -21,19 +21,29 @@ def _dev(torch, a, dt):
     return torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
 
 
-def test_noalloc_query_matches_workspace_query_twice(rambo_lib):
+@pytest.mark.parametrize("tuning", [dict(query_path=0), dict(query_path=1),
+                                    dict(query_path=2, bin_region_kib=256)])
+def test_noalloc_query_matches_workspace_query_and_oracle_twice(rambo_lib, tuning):
+    # each query path the tuning can pick (path 2 with regions large enough
+    # that its record bins fit the static scratch), two different batches in
+    # a row: the second call must not see what the first left in the array
     import torch
+    import oracle
     p = synth.Params(K=150, B=24, R=3, m=1 << 16, eta=2, k=31, seed=3)
     rng = np.random.default_rng(41)
     corpus = synth.family_corpus(rng, p, n_seeds=10, doc_len=2000, sub_rate=0.01)
     idx = rambo_lib.Index(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
     idx.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
+    idx.set_tuning(**tuning)
+    o = oracle.Rambo(p.K, p.B, p.R, p.m, p.eta, p.k, p.seed)
+    o.insert_batch(corpus.doc_ids, corpus.packed, corpus.offsets)
     lib = rambo_lib.load()
     stream = torch.cuda.current_stream()
-    # two different batches in a row: the second call must not see the first's state
     for call, n in enumerate((300, 211)):
         q = synth.sample_queries(rng, corpus, rng.integers(20, 600, size=n), 0.6)
         packed, offs = _dev(torch, q.packed, np.uint8), _dev(torch, q.offsets, np.int64)
+        if tuning["query_path"] == 2:  # the binned layout fits the scratch for this batch
+            assert idx.workspace_bytes("seqs", n, packed.numel()) <= STATIC_SCRATCH_BYTES
         want = idx.query_seqs_dev(packed, offs)
         idx.sync()
         got = torch.full((n, idx.W), -1, dtype=torch.int32, device="cuda")
@@ -42,6 +52,8 @@ def test_noalloc_query_matches_workspace_query_twice(rambo_lib):
         assert rc == rambo_lib.RAMBO_OK, f"call {call}: {rc}"
         idx.sync()
         assert torch.equal(got, want), f"call {call} differs from rambo_query_seqs_dev"
+        assert np.array_equal(rambo_lib.as_u32(got), o.query_seqs(q.packed, q.offsets)), \
+            f"call {call} differs from the oracle"
 
 
 def test_noalloc_rejects_batches_beyond_the_scratch(rambo_lib):
