@@ -31,7 +31,7 @@ from . import rambo
 def route(K: int, shards: int, seed: int = 0) -> np.ndarray:
     """tau: document -> shard, a seeded splitmix64-style integer hash (host-side
     routing only; it is not part of any index)."""
-    x = (np.arange(K, dtype=np.uint64) + np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15))
+    x = np.arange(K, dtype=np.uint64) + np.uint64((seed * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF)
     x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
     x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
     x = x ^ (x >> np.uint64(31))
