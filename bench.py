@@ -305,13 +305,16 @@ def serving_section(idx, corpus, n_req: int, fracs=(0.1, 0.25, 0.5, 0.75, 0.9, 1
     same = bool(np.array_equal(plain_sat.answers, cont_sat.answers))
     ps, cs = plain_sat.summary(), cont_sat.summary()
     sat_rps = n_req / ps["wall_s"]
+    one = serve.one_batch_rate(idx, reqs0)
     out = {"requests_per_rate": n_req, "length_dist": "log-normal median 300 bp, sigma 1, [31, 10^4]",
            "rates_relative_to": "plain 256-request batches at saturation",
            "saturation": {"plain_batch256": {"requests_per_s": sat_rps, "bp_per_s": ps["bp_per_s"],
                                              "p50_ms": ps["p50_ms"], "p99_ms": ps["p99_ms"]},
                           "continuous": {"requests_per_s": n_req / cs["wall_s"], "bp_per_s": cs["bp_per_s"],
                                          "p50_ms": cs["p50_ms"], "p99_ms": cs["p99_ms"],
-                                         "batches": cs["batches"]}},
+                                         "batches": cs["batches"],
+                                         "frac_of_one_batch_device_rate": cs["bp_per_s"] / one["bp_per_s"]},
+                          "one_batch_device": one},
            "rates": []}
     for f in fracs:
         arrivals = np.cumsum(rng.exponential(1.0 / (f * sat_rps), size=n_req))

@@ -248,6 +248,31 @@ def plain_batched(idx, requests: list[Request], batch_size: int, max_batch_bytes
                        {"mode": "plain", "batch_size": batch_size})
 
 
+def one_batch_rate(idx, requests: list[Request], reps: int = 3) -> dict:
+    """The device's batched rate on a trace: every request in one
+    query_ranges_dev call, inputs already on the device, timed with CUDA
+    events (best of reps) -- the ceiling a server of this trace can approach."""
+    import torch
+    tr = _Trace(requests, max(r.packed.size for r in requests))
+    n = tr.n
+    b = torch.empty(n, dtype=torch.int64)
+    e = torch.empty(n, dtype=torch.int64)
+    tr.ranges(0, n, b.numpy(), e.numpy())
+    dev = torch.device(f"cuda:{idx.device}")
+    dp, db, de = tr.arena.to(dev), b.to(dev), e.to(dev)
+    out = idx.query_ranges_dev(dp, db, de)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        e0.record()
+        idx.query_ranges_dev(dp, db, de, out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1))
+    return {"ms": best, "bp_per_s": tr.bases / (best / 1e3), "requests_per_s": n / (best / 1e3)}
+
+
 def make_requests(corpus, arrivals: np.ndarray, lengths: np.ndarray, rng, frac_from_docs=0.7,
                   err_rate=0.001) -> list[Request]:
     """Requests shaped like the serving workload: 70% substrings of documents
