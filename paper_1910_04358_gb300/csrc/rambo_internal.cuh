@@ -301,7 +301,7 @@ bool fused_supported(const Geometry &g);
 // 64 bytes): records in nb x G sub-bins of cap records each (bin = region
 // pos >> shift, G = the scatter's grid: one sub-bin per bin and block).
 constexpr uint32_t BINNED_TILE_RECS = 4096;  // probe records per scatter tile
-constexpr uint32_t BINNED_ITEM_RECS = 256;   // records per probe-pass work item
+constexpr uint32_t BINNED_ITEM_RECS = 512;   // records per probe-pass work item
 struct BinnedArgs {
     ProbeArgs p;                    // index, hashing, batch; kcum = the tile prefix
                                     // (tiles of `tile` k-mers, every query with k-mers);
@@ -314,7 +314,7 @@ struct BinnedArgs {
     uint32_t nb, shift;
     uint32_t G;                     // scatter grid (binned_scatter_grid)
     uint32_t tile;                  // k-mers per scatter tile (binned_tile_kmers)
-    uint32_t depth;                 // probe pass: gathers a lane keeps in flight (4, 6, 8)
+    uint32_t depth;                 // probe pass: group gathers a lane keeps in flight (2, 4, 8)
     uint32_t cps;                   // work items per sub-bin: ceil(cap / BINNED_ITEM_RECS)
 };
 bool binned_supported(const Geometry &g);

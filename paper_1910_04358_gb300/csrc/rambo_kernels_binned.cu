@@ -217,92 +217,211 @@ __device__ __forceinline__ void flush_run(uint32_t *acc, uint32_t q, uint32_t Gw
     }
 }
 
-// Probe pass.  A group of GW words is read by L = GW/4 lanes (one lane for
-// groups of up to 16 bytes), 16 bytes each; a warp has 32/L lane groups.
-// Work item c = chunk (c % cps) of sub-bin (c / cps): 256 consecutive
-// records; lane group j walks its 256/(32/L) consecutive records of it in
-// order, keeping the AND of the current run (records of one query) in
-// registers, with the gathers of the next D records in flight.  A run is
-// folded into its query's mask where the query changes and at the end of
-// the walk.
+// Shared-memory stride (words) of one staged group: groups of 16 bytes and
+// more are padded by 16 bytes, so that the 16-byte accesses of 8 consecutive
+// lanes fall in distinct banks.
+template <int GW>
+__host__ __device__ constexpr int slot_words() { return GW >= 4 ? GW + 4 : GW; }
+
+// Copies the GW-word group at `src` into shared memory `dst` (cp.async).
+template <int GW>
+__device__ __forceinline__ void stage_group(uint32_t *dst, const uint32_t *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if constexpr (GW >= 4) {
+#pragma unroll
+        for (int w = 0; w < GW; w += 4)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 4 * w), "l"(src + w) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(GW * 4) : "memory");
+    }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int GW>
+__device__ __forceinline__ void and_staged(uint32_t (&run)[GW], const uint32_t *g) {
+    if constexpr (GW >= 4) {
+#pragma unroll
+        for (int w = 0; w < GW; w += 4) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(g + w);
+            run[w] &= v.x;
+            run[w + 1] &= v.y;
+            run[w + 2] &= v.z;
+            run[w + 3] &= v.w;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < GW; ++w) run[w] &= g[w];
+    }
+}
+
+template <int GW>
+__device__ __forceinline__ void put_run(uint32_t *dst, const uint32_t (&run)[GW]) {
+    if constexpr (GW >= 4) {
+#pragma unroll
+        for (int w = 0; w < GW; w += 4)
+            *reinterpret_cast<uint4 *>(dst + w) = make_uint4(run[w], run[w + 1], run[w + 2], run[w + 3]);
+    } else {
+#pragma unroll
+        for (int w = 0; w < GW; ++w) dst[w] = run[w];
+    }
+}
+
+// Folds queued runs [0, n) (rq[i] their queries) into their queries' masks:
+// LPR lanes per run, one 64-bit word each (32-bit for 4-byte groups), so a
+// run of a 64-byte group is one coalesced instruction.
+template <int GW>
+__device__ __forceinline__ void drain_runs(uint32_t *acc, const uint32_t *runs, const uint32_t *rq,
+                                           uint32_t n, int lane) {
+    constexpr int LPR = GW >= 16 ? 8 : (GW >= 2 ? GW / 2 : 1);
+    constexpr int RPI = 32 / LPR;
+    for (uint32_t i0 = 0; i0 < n; i0 += RPI) {
+        const uint32_t i = i0 + lane / LPR;
+        if (i < n) {
+            const uint32_t q = rq[i];
+            const uint32_t *r = runs + (size_t)i * slot_words<GW>();
+            if constexpr (GW == 1) {
+                if (r[0] != FULL) atomicAnd(acc + q, r[0]);
+            } else {
+                const uint32_t w = (lane % LPR) * 2;
+                const unsigned long long v = ((unsigned long long)r[w + 1] << 32) | r[w];
+                if (v != ~0ull) atomicAnd(reinterpret_cast<unsigned long long *>(acc + (uint64_t)q * GW + w), v);
+            }
+        }
+    }
+}
+
+// Probe pass.  Work item c = chunk (c % cps) of sub-bin (c / cps):
+// BINNED_ITEM_RECS consecutive records, 32 per lane.  A lane walks its
+// records in order: the group of each record is copied into the lane's
+// shared-memory ring (cp.async, no registers held) D records ahead of its
+// use, and the AND of the current run (records of one query) is kept in
+// registers.  A run ends where the query changes or the lane's records end;
+// it is queued in the warp's shared memory, and once 16 or more are queued
+// the warp folds them into the queries' masks together, one coalesced
+// atomicAnd instruction per mask row.
+constexpr int PROBE_WARPS = 4;
+constexpr int PROBE_PER = 16;     // records per lane and item
+constexpr int PROBE_QUEUE = 48;   // run queue: drained at 16, at most 32 added a step
+
 template <int GW, int D>
-__global__ void __launch_bounds__(BIN_THREADS) k_bin_probe(BinnedArgs a) {
-    constexpr int L = GW >= 4 ? GW / 4 : 1;   // lanes per group
-    constexpr int SW = GW >= 4 ? 4 : GW;      // words per lane
-    constexpr int PERG = BINNED_ITEM_RECS / (32 / L);  // records per lane group and item
-    constexpr int RPL = PERG / L;             // records each lane loads (8)
+__host__ __device__ constexpr size_t probe_smem() {
+    return (size_t)PROBE_WARPS * ((size_t)D * 32 * slot_words<GW>() * 4 +           // group ring
+                                  (size_t)PROBE_QUEUE * slot_words<GW>() * 4 +       // queued runs
+                                  (size_t)PROBE_QUEUE * 4);                          // their queries
+}
+
+template <int GW, int D>
+__global__ void __launch_bounds__(PROBE_WARPS * 32) k_bin_probe(BinnedArgs a) {
+    constexpr int SG = slot_words<GW>();
+    static_assert(BINNED_ITEM_RECS == 32 * PROBE_PER, "work item = 32 lanes x PROBE_PER records");
+    extern __shared__ __align__(16) uint32_t probe_smem_u32[];
     const int lane = threadIdx.x & 31;
-    const int grp = lane / L, sub = lane % L;
-    const uint32_t word0 = (uint32_t)sub * SW;
-    const uint64_t warp = (uint64_t)blockIdx.x * (BIN_THREADS / 32) + (threadIdx.x >> 5);
-    const uint64_t nwarps = (uint64_t)gridDim.x * (BIN_THREADS / 32);
+    const int wib = threadIdx.x >> 5;
+    uint32_t *ring = probe_smem_u32 + (size_t)wib * (D * 32 * SG + PROBE_QUEUE * SG + PROBE_QUEUE);
+    uint32_t *runs = ring + D * 32 * SG;
+    uint32_t *rq = runs + PROBE_QUEUE * SG;
+    uint32_t *slot0 = ring + (size_t)lane * SG;  // this lane's slot d is slot0 + d * 32 * SG
+    const uint64_t warp = (uint64_t)blockIdx.x * PROBE_WARPS + wib;
+    const uint64_t nwarps = (uint64_t)gridDim.x * PROBE_WARPS;
     const uint64_t items = (uint64_t)a.nb * a.G * a.cps;
     uint32_t *acc = a.p.acc;
     const uint32_t *index = a.p.index;
+    uint32_t queued = 0;  // warp-uniform
     for (uint64_t c = warp; c < items; c += nwarps) {
         const uint64_t sb = c / a.cps;
         const uint32_t cnt = a.sub_count[sb];
         const uint32_t chunk0 = (uint32_t)(c - sb * a.cps) * BINNED_ITEM_RECS;
         if (chunk0 >= cnt) continue;  // warp-uniform: an empty chunk
-        const uint32_t gfirst = chunk0 + (uint32_t)grp * PERG;
-        const uint32_t ng = gfirst < cnt ? (cnt - gfirst < (uint32_t)PERG ? cnt - gfirst : (uint32_t)PERG) : 0u;
+        const uint32_t first = chunk0 + (uint32_t)lane * PROBE_PER;
+        const uint32_t mine = first < cnt ? (cnt - first < (uint32_t)PROBE_PER ? cnt - first : (uint32_t)PROBE_PER) : 0u;
         const unsigned long long *rec =
-            reinterpret_cast<const unsigned long long *>(a.records) + sb * a.cap + gfirst;
-        // this lane's share of the group's records: sub, sub + L, ...
-        unsigned long long r[RPL];
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-            const uint32_t i = (uint32_t)(sub + L * k);
-            r[k] = i < ng ? __ldcs(rec + i) : ~0ull;
-        }
-        // record i of the group, seen by all of its lanes
-        auto rec_at = [&](int i) -> unsigned long long {
-            return __shfl_sync(FULL, r[i / L], grp * L + i % L);
-        };
-        Slice<SW> buf[D];
+            reinterpret_cast<const unsigned long long *>(a.records) + sb * a.cap + first;
+        unsigned long long rr[D];  // the records whose groups are in flight
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const unsigned long long x = rec_at(i);
-            if (i < PERG && x != ~0ull) buf[i] = ld_slice<SW>(index + (x >> 32) * GW + word0);
-            else slice_ones(buf[i]);
+            rr[i] = (uint32_t)i < mine ? __ldg(rec + i) : ~0ull;
+            if (rr[i] != ~0ull) stage_group<GW>(slot0 + i * 32 * SG, index + (rr[i] >> 32) * GW);
+            cp_commit();
         }
         uint32_t cq = NONE;
-        Slice<SW> run;
-        slice_ones(run);
+        uint32_t run[GW];
 #pragma unroll
-        for (int i = 0; i < PERG; ++i) {
-            const unsigned long long x = rec_at(i);
-            const uint32_t q = x != ~0ull ? (uint32_t)x : NONE;
-            if (q != cq) {
-                if (cq != NONE) flush_run<SW>(acc, cq, GW, word0, run);
-                cq = q;
-                slice_ones(run);
-            }
-            slice_and(run, buf[i % D]);
-            if (i + D < PERG) {
-                const unsigned long long y = rec_at(i + D);
-                if (y != ~0ull) buf[i % D] = ld_slice<SW>(index + (y >> 32) * GW + word0);
-                else slice_ones(buf[i % D]);
+        for (int w = 0; w < GW; ++w) run[w] = FULL;
+#pragma unroll 1
+        for (int i0 = 0; i0 < PROBE_PER; i0 += D) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int i = i0 + d;
+                cp_wait<D - 1>();  // record i's group has landed in slot d
+                const unsigned long long x = rr[d];
+                const uint32_t q = x != ~0ull ? (uint32_t)x : NONE;
+                const bool closes = cq != NONE && q != cq;
+                const uint32_t ballot = __ballot_sync(FULL, closes);
+                if (closes) {
+                    const uint32_t at = queued + __popc(ballot & ((1u << lane) - 1u));
+                    rq[at] = cq;
+                    put_run<GW>(runs + at * SG, run);
+                }
+                queued += __popc(ballot);
+                if (q != cq) {
+                    cq = q;
+#pragma unroll
+                    for (int w = 0; w < GW; ++w) run[w] = FULL;
+                }
+                if (x != ~0ull) and_staged<GW>(run, slot0 + d * 32 * SG);
+                // the slot is free again: the record D ahead
+                const uint32_t nx = (uint32_t)(i + D);
+                rr[d] = nx < mine ? __ldg(rec + nx) : ~0ull;
+                if (rr[d] != ~0ull) stage_group<GW>(slot0 + d * 32 * SG, index + (rr[d] >> 32) * GW);
+                cp_commit();
+                if (queued >= 16) {
+                    __syncwarp();
+                    drain_runs<GW>(acc, runs, rq, queued, lane);
+                    __syncwarp();
+                    queued = 0;
+                }
             }
         }
-        if (cq != NONE) flush_run<SW>(acc, cq, GW, word0, run);
+        // the lanes' last runs
+        const bool last = cq != NONE;
+        const uint32_t ballot = __ballot_sync(FULL, last);
+        if (last) {
+            const uint32_t at = queued + __popc(ballot & ((1u << lane) - 1u));
+            rq[at] = cq;
+            put_run<GW>(runs + at * SG, run);
+        }
+        queued += __popc(ballot);
+        if (queued >= 16) {
+            __syncwarp();
+            drain_runs<GW>(acc, runs, rq, queued, lane);
+            __syncwarp();
+            queued = 0;
+        }
     }
+    __syncwarp();
+    drain_runs<GW>(acc, runs, rq, queued, lane);
+    cp_wait<0>();
 }
 
 template <int GW, int D>
 cudaError_t launch_probe_d(const BinnedArgs &a, int sm_count, cudaStream_t s) {
-    int occ = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bin_probe<GW, D>, BIN_THREADS, 0);
+    constexpr size_t smem = probe_smem<GW, D>();
+    cudaError_t e = cudaFuncSetAttribute(k_bin_probe<GW, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_bin_probe<GW, D><<<(occ > 0 ? occ : 1) * sm_count, BIN_THREADS, 0, s>>>(a);
+    int occ = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bin_probe<GW, D>, PROBE_WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    k_bin_probe<GW, D><<<(occ > 0 ? occ : 1) * sm_count, PROBE_WARPS * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int GW>
 cudaError_t launch_probe_pass(const BinnedArgs &a, int sm_count, cudaStream_t s) {
     switch (a.depth) {
+        case 2: return launch_probe_d<GW, 2>(a, sm_count, s);
         case 4: return launch_probe_d<GW, 4>(a, sm_count, s);
-        case 6: return launch_probe_d<GW, 6>(a, sm_count, s);
         default: return launch_probe_d<GW, 8>(a, sm_count, s);
     }
 }
@@ -327,7 +446,7 @@ bool binned_supported(const Geometry &g) { return g.Gw == 1 || g.Gw == 2 || g.Gw
 
 uint32_t binned_records_per_item() { return BINNED_ITEM_RECS; }
 
-uint32_t binned_depth(uint32_t rows) { return (rows == 0 || rows == 1) ? 4u : rows == 2 ? 6u : 8u; }
+uint32_t binned_depth(uint32_t rows) { return rows == 1 ? 2u : (rows == 0 || rows == 2) ? 4u : 8u; }
 
 uint32_t binned_tile_kmers(const Geometry &g) {
     const uint32_t t = BINNED_TILE_RECS / (g.eta ? g.eta : 1);
@@ -363,7 +482,7 @@ int binned_launches() { return 3; }
 cudaError_t launch_binned(const BinnedArgs &a, const Geometry &g, int sm_count, cudaStream_t s) {
     if (!binned_supported(g) || a.tile == 0 || (uint64_t)a.tile * a.p.eta > BINNED_TILE_RECS ||
         a.nb == 0 || a.nb > BIN_MAX || a.G == 0 || (a.cap & 1) ||
-        (a.depth != 4 && a.depth != 6 && a.depth != 8) ||
+        (a.depth != 2 && a.depth != 4 && a.depth != 8) ||
         a.cps != (uint32_t)((a.cap + BINNED_ITEM_RECS - 1) / BINNED_ITEM_RECS))
         return cudaErrorInvalidValue;
     if (a.p.n == 0) return cudaSuccess;
