@@ -222,7 +222,7 @@ int apply_bytetab(rambo_t *h) {
 
 // Workspace layouts (offsets are 256-byte aligned).
 struct SeqWs {
-    size_t kcum, bsum, acc, qcnt, slist, done, total;
+    size_t kcum, bsum, acc, qcnt, slist, done, heavy, total;
 };
 SeqWs seq_ws(const Geometry &g, uint64_t n) {
     SeqWs w;
@@ -232,7 +232,8 @@ SeqWs seq_ws(const Geometry &g, uint64_t n) {
     w.qcnt = w.acc + align_up(n * (uint64_t)g.Gw * 4);
     w.slist = w.qcnt + ALIGN;
     w.done = w.slist + align_up(n * 4);
-    w.total = w.done + align_up(n * 4);
+    w.heavy = w.done + align_up(n * 4);
+    w.total = w.heavy + align_up(n * 4);
     return w;
 }
 
@@ -413,6 +414,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
         qs.short_list = reinterpret_cast<uint32_t *>(w + L.slist);
         qs.tile_prefix = kcum;
         qs.done = reinterpret_cast<uint32_t *>(w + L.done);
+        qs.heavy = reinterpret_cast<uint32_t *>(w + L.heavy);
         qs.tile = h->tune.fused_tile_kmers;
         qs.short_max = h->tune.fused_short_max;
         qs.user_bases = packed_bytes * 4;
@@ -425,7 +427,7 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
             RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s,
                                          qs.tile, qs.short_max));
         }
-        StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 2);
+        StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, 3);
         uint32_t ctas = h->tune.probe_ctas_per_sm;
         if (fused_ctas_cap && (ctas == 0 || ctas > fused_ctas_cap)) ctas = fused_ctas_cap;
         const int go = ctas ? (int)(h->sm_count * ctas) : 0;

@@ -284,10 +284,11 @@ cudaError_t launch_probe_kmers(const ProbeArgs &a, const Geometry &g, int sm_cou
                                bool staged);
 // Work queues of the persistent fused query (workspace arrays).
 struct FusedQueues {
-    uint32_t *counters;      // 4 words, zeroed by the launcher
+    uint32_t *counters;      // 8 words, zeroed by the launcher
     uint32_t *short_list;    // n
     const uint64_t *tile_prefix;  // n+1: exclusive prefix of long-query tile counts
     uint32_t *done;          // n
+    uint32_t *heavy;         // n: queries expanded by the second launch
     uint32_t tile;           // k-mers per long tile
     uint32_t short_max;      // longest short query (k-mers)
     uint64_t user_bases;     // bases addressable from the caller's packed pointer
@@ -328,7 +329,9 @@ uint32_t binned_bins(const Geometry &g, uint64_t region_bytes, uint32_t *shift);
 int binned_launches();
 cudaError_t launch_binned(const BinnedArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 
-// p.acc is unused (the bucket masks of long queries are e.acc).
+// p.acc is unused (the bucket masks of long queries, and of queries with too
+// many passing buckets to expand in place, are e.acc).  Two launches after
+// the prep: the persistent query and the heavy queries' expansion.
 cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry &g,
                          const FusedQueues &qs, int grid_override, int sm_count, cudaStream_t s);
 

@@ -28,9 +28,11 @@ constexpr int FUSED_THREADS = 256;
 struct FusedArgs {
     ProbeArgs p;                 // index, geometry, batch (kcum unused)
     uint32_t *counters;          // [0] short count [1] short head [2..3] 64-bit tile head
+                                 // [4] heavy count
     uint32_t *short_list;        // n
     const uint64_t *tile_prefix; // n+1
     uint32_t *done;              // n (long queries)
+    uint32_t *heavy;             // n: queries whose expansion is left to k_fused_heavy
     uint32_t tile;               // k-mers per long tile
     uint32_t short_max;          // k-mers of the longest short query
     uint64_t user_bases;         // bases addressable from the caller's pointer
@@ -261,7 +263,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, (LPG >= 4 || ASYNC) ? 3 : 2) k_
             __threadfence();
             for (uint32_t w = lane; w < f.p.Gw; w += 32) bm[w] = __ldcg(f.e.acc + q * f.p.Gw + w);
             __syncwarp();
-            expand_query<C>(f.e, bm, q, chunks, lane, list);
+            expand_query<C>(f.e, bm, q, chunks, lane, list, f.heavy, f.counters + 4,
+                            const_cast<uint32_t *>(f.e.acc));
             __syncwarp();
         }
     }
@@ -295,8 +298,27 @@ __global__ void __launch_bounds__(FUSED_THREADS, (LPG >= 4 || ASYNC) ? 3 : 2) k_
 #pragma unroll
             for (int w = 0; w < SW; ++w) bm[word0 + w] = sl.w[w];
         __syncwarp();
-        expand_query<C>(f.e, bm, q, chunks, lane, list);
+        expand_query<C>(f.e, bm, q, chunks, lane, list, f.heavy, f.counters + 4,
+                        const_cast<uint32_t *>(f.e.acc));
         __syncwarp();
+    }
+}
+
+// The heavy queries' answers (more passing buckets than a warp's list
+// holds): one warp per (query, chunk of 32*C answer words), grid-stride, the
+// bucket mask read from acc.
+template <int C>
+__global__ void __launch_bounds__(256) k_fused_heavy(FusedArgs f) {
+    const uint32_t count = f.counters[4];
+    const uint32_t chunks = (f.e.W + 32 * C - 1) / (32 * C);
+    const uint64_t units = (uint64_t)count * chunks;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const uint64_t nwarps = (uint64_t)gridDim.x * 8;
+    for (uint64_t u = warp; u < units; u += nwarps) {
+        const uint64_t q = f.heavy[u / chunks];
+        const uint32_t c = (uint32_t)(u % chunks);
+        expand_one<C>(f.e, f.e.acc + q * f.p.Gw, q, c * 32 * C + lane, lane);
     }
 }
 
@@ -313,6 +335,9 @@ cudaError_t launch_fused_t(const FusedArgs &f, int grid_override, int sm_count, 
     static int occ = blocks_per_sm(k_fused<SW, LPG, ETA, C, ASYNC>, FUSED_THREADS, smem);
     const int grid = grid_override > 0 ? grid_override : sm_count * occ;
     k_fused<SW, LPG, ETA, C, ASYNC><<<grid, FUSED_THREADS, smem, s>>>(f);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fused_heavy<C><<<sm_count * 4, 256, 0, s>>>(f);
     return cudaGetLastError();
 }
 
@@ -350,6 +375,7 @@ cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry
     f.short_list = qs.short_list;
     f.tile_prefix = qs.tile_prefix;
     f.done = qs.done;
+    f.heavy = qs.heavy;
     f.tile = qs.tile;
     f.short_max = qs.short_max;
     f.user_bases = qs.user_bases;
@@ -357,7 +383,7 @@ cudaError_t launch_fused(const ProbeArgs &p, const ExpandArgs &e, const Geometry
     f.early_exit = qs.early_exit;
     f.segment = qs.segment;
     f.probed = qs.probed;
-    cudaError_t err = cudaMemsetAsync(qs.counters, 0, 4 * sizeof(uint32_t), s);
+    cudaError_t err = cudaMemsetAsync(qs.counters, 0, 8 * sizeof(uint32_t), s);
     if (err != cudaSuccess) return err;
     if (p.n == 0) return cudaSuccess;
     k_fused_prep<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(f);

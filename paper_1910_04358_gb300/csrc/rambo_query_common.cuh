@@ -182,18 +182,23 @@ __device__ __forceinline__ void expand_unit_sparse(const ExpandArgs &a, const ui
         for (int c = 0; c < C; ++c) o[c] = 0;
         bool any = false;
         for (uint32_t j = 0; j < NJ; ++j) {
-            uint32_t v = row_byte(bm, a.Gw, a.B, r, j);
-            any |= v != 0;
-            while (v) {
-                const uint32_t b = 8 * j + __ffs(v) - 1;
-                v &= v - 1;
-                const uint32_t *row = a.docbits + (uint64_t)(r * a.B + b) * a.W;
+            const uint32_t v = row_byte(bm, a.Gw, a.B, r, j);
+            if (!v) continue;
+            any = true;
+            // the rows of the byte's set bits, all loads issued before any is used
+            const uint32_t *row0 = a.docbits + (uint64_t)(r * a.B + 8 * j) * a.W;
+            uint32_t val[8][C];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const uint32_t w = w0 + 32 * c;
-                    if (w < a.W) o[c] |= __ldg(row + w);
+                    val[t][c] = ((v >> t) & 1u) && w < a.W ? __ldg(row0 + (uint64_t)t * a.W + w) : 0u;
                 }
-            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+#pragma unroll
+                for (int c = 0; c < C; ++c) o[c] |= val[t][c];
         }
         uint32_t nz = 0;
 #pragma unroll
@@ -372,15 +377,29 @@ __device__ __forceinline__ void expand_unit_list(const ExpandArgs &a, const uint
 // into `list` (EXPAND_LIST_MAX words of the warp's shared memory) and each
 // chunk walks them; otherwise, or when more buckets pass, each chunk scans
 // the mask itself.
+//
+// With a heavy list (the persistent fused query), a query with more passing
+// buckets than the list holds is not expanded here: its mask is stored at
+// acc_out[q] and q is appended to heavy_list, and a later launch spreads its
+// chunks over all warps (one such query costs R*B/8 byte scans and a row per
+// passing bucket for every chunk, which one warp would take alone).
 template <int C>
 __device__ __forceinline__ void expand_query(const ExpandArgs &a, const uint32_t *bm, uint64_t q,
-                                             uint32_t chunks, int lane, uint32_t *list) {
+                                             uint32_t chunks, int lane, uint32_t *list,
+                                             uint32_t *heavy_list = nullptr, uint32_t *heavy_count = nullptr,
+                                             uint32_t *acc_out = nullptr) {
     if (chunks > 1 && !a.tab) {
         bool dead = false;
         const uint32_t n = bucket_list(bm, a.R, a.B, list, lane, &dead);
         if (n <= EXPAND_LIST_MAX) {
             for (uint32_t c = 0; c < chunks; ++c) expand_unit_list<C>(a, list, n, dead, q, c * 32 * C + lane);
             __syncwarp();  // the list is the next query's
+            return;
+        }
+        if (heavy_list) {
+            for (uint32_t w = lane; w < a.Gw; w += 32) acc_out[q * a.Gw + w] = bm[w];
+            if (lane == 0) heavy_list[atomicAdd(heavy_count, 1u)] = (uint32_t)q;
+            __syncwarp();
             return;
         }
     }
