@@ -305,20 +305,127 @@ __global__ void __launch_bounds__(FUSED_THREADS, (LPG >= 4 || ASYNC) ? 3 : 2) k_
 }
 
 // The heavy queries' answers (more passing buckets than a warp's list
-// holds): one warp per (query, chunk of 32*C answer words), grid-stride, the
-// bucket mask read from acc.
+// holds): one warp per (query, chunk of 32*C answer words), grid-stride.
+// The warp decodes the query's passing buckets (bucket-space mask in acc)
+// into a sorted list of bucket indices r*B + b in its shared memory, then
+// ORs the rows of each repetition, several rows in flight, and ANDs the
+// repetitions (Algorithm 2's union per repetition and intersection over R).
+constexpr int HEAVY_WARPS = 8;
+
+// Indices i = r*B + b of the set bits of bm (bits below R*B), increasing,
+// into list; returns how many.  *dead: some repetition has none.
+__device__ __forceinline__ uint32_t bucket_list_all(const uint32_t *bm, uint32_t R, uint32_t B, uint16_t *list,
+                                                    int lane, bool *dead) {
+    const uint32_t RB = R * B;
+    const uint32_t nw = (RB + 31) / 32;
+    uint32_t total = 0;
+    for (uint32_t base = 0; base < nw; base += 32) {
+        const uint32_t w = base + lane;
+        uint32_t v = w < nw ? __ldg(bm + w) : 0u;
+        if (w == nw - 1 && (RB & 31)) v &= (1u << (RB & 31)) - 1u;
+        const uint32_t cnt = __popc(v);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += o;
+        }
+        uint32_t at = total + incl - cnt;
+        while (v) {
+            list[at++] = (uint16_t)(32 * w + __ffs(v) - 1);
+            v &= v - 1;
+        }
+        total += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    // every repetition present?  count the repetition changes along the list
+    uint32_t reps = 0;
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        bool first = false;
+        if (t < total) first = t == 0 || list[t - 1] / B != list[t] / B;
+        reps += __popc(__ballot_sync(FULL, first));
+    }
+    *dead = reps < R;
+    return total;
+}
+
 template <int C>
-__global__ void __launch_bounds__(256) k_fused_heavy(FusedArgs f) {
+__device__ __forceinline__ void expand_heavy_unit(const ExpandArgs &a, const uint16_t *list, uint32_t n,
+                                                  bool dead, uint64_t q, uint32_t w0) {
+    constexpr int U = 4;  // rows in flight
+    uint32_t res[C], o[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        res[c] = dead ? 0u : FULL;
+        o[c] = 0;
+    }
+    if (!dead && n) {
+        uint32_t rep = list[0] / a.B;
+        bool empty = false;
+        for (uint32_t t0 = 0; t0 < n && !empty; t0 += U) {
+            uint32_t idx[U], val[U][C];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                idx[u] = t0 + u < n ? list[t0 + u] : NONE;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t w = w0 + 32 * c;
+                    val[u][c] = idx[u] != NONE && w < a.W ? __ldg(a.docbits + (uint64_t)idx[u] * a.W + w) : 0u;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (idx[u] == NONE) break;
+                const uint32_t r = idx[u] / a.B;
+                if (r != rep) {  // a repetition is complete
+                    uint32_t nz = 0;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        res[c] &= o[c];
+                        o[c] = 0;
+                        nz |= res[c];
+                    }
+                    rep = r;
+                    if (!__any_sync(FULL, nz)) empty = true;
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) o[c] |= val[u][c];
+            }
+        }
+        if (!empty)
+#pragma unroll
+            for (int c = 0; c < C; ++c) res[c] &= o[c];
+        else
+#pragma unroll
+            for (int c = 0; c < C; ++c) res[c] = 0;
+    }
+    uint32_t *out = a.out + q * a.W;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const uint32_t w = w0 + 32 * c;
+        if (w < a.W) out[w] = res[c];
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(HEAVY_WARPS * 32) k_fused_heavy(FusedArgs f) {
+    extern __shared__ uint16_t heavy_lists[];  // HEAVY_WARPS x R*B
     const uint32_t count = f.counters[4];
     const uint32_t chunks = (f.e.W + 32 * C - 1) / (32 * C);
     const uint64_t units = (uint64_t)count * chunks;
     const int lane = threadIdx.x & 31;
-    const uint64_t warp = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const uint64_t nwarps = (uint64_t)gridDim.x * 8;
+    const int wib = threadIdx.x >> 5;
+    uint16_t *list = heavy_lists + (size_t)wib * f.e.R * f.e.B;
+    const uint64_t warp = (uint64_t)blockIdx.x * HEAVY_WARPS + wib;
+    const uint64_t nwarps = (uint64_t)gridDim.x * HEAVY_WARPS;
     for (uint64_t u = warp; u < units; u += nwarps) {
         const uint64_t q = f.heavy[u / chunks];
         const uint32_t c = (uint32_t)(u % chunks);
-        expand_one<C>(f.e, f.e.acc + q * f.p.Gw, q, c * 32 * C + lane, lane);
+        bool dead = false;
+        const uint32_t n = bucket_list_all(f.e.acc + q * f.p.Gw, f.e.R, f.e.B, list, lane, &dead);
+        expand_heavy_unit<C>(f.e, list, n, dead, q, c * 32 * C + lane);
+        __syncwarp();  // the list is the next unit's
     }
 }
 
@@ -337,7 +444,12 @@ cudaError_t launch_fused_t(const FusedArgs &f, int grid_override, int sm_count, 
     k_fused<SW, LPG, ETA, C, ASYNC><<<grid, FUSED_THREADS, smem, s>>>(f);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_fused_heavy<C><<<sm_count * 4, 256, 0, s>>>(f);
+    const size_t hsmem = (size_t)HEAVY_WARPS * f.e.R * f.e.B * sizeof(uint16_t);
+    if (hsmem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_fused_heavy<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+        if (e != cudaSuccess) return e;
+    }
+    k_fused_heavy<C><<<sm_count * 4, HEAVY_WARPS * 32, hsmem, s>>>(f);
     return cudaGetLastError();
 }
 
