@@ -42,7 +42,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 CSRC = os.path.join(ROOT, "paper_1910_04358_gb300", "csrc")
 KERNEL_SRC = {"k_fused": "rambo_kernels_fused.cu", "k_probe_seqs": "rambo_kernels_probe.cu",
-              "k_binned": "rambo_kernels_binned.cu"}
+              "k_binned": "rambo_kernels_binned.cu", "k_segments": "rambo_kernels_segments.cu"}
 SECTOR = 32
 STAGES_ALL = ("prefix", "register", "insert", "probe_seqs", "probe_kmers", "expand")
 
@@ -940,7 +940,7 @@ def run_ours(args):
         alg_bytes += q.n * idx.W * 4
     peak, peak_src = measured_peak_gbs()
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-    src_key = {0: "k_probe_seqs", 1: "k_fused", 2: "k_binned"}[path]
+    src_key = {0: "k_probe_seqs", 1: "k_fused", 2: "k_binned", 3: "k_segments"}[path]
     traffic = measured_traffic(args.workload, src_key, n_seq_kmers)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
@@ -955,7 +955,8 @@ def run_ours(args):
                 "traffic_source": ("profiles/traffic.json: ncu DRAM bytes per k-mer on a reduced "
                                    "geometry of this kernel, scaled by the batch's k-mers") if traffic else None,
                 "kernel": {0: "k_probe_seqs", 1: "k_fused_prep+k_fused",
-                           2: "k_bin_tiles+k_bin_scatter+k_bin_probe"}[path],
+                           2: "k_bin_tiles+k_bin_scatter+k_bin_probe",
+                           3: "k_seg_cut+k_seg_scan+k_seg_place+segment prefix+k_seg_chunks+k_seg_probe"}[path],
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "bytes_per_kmer": probe_bytes_per_kmer(info), "avg_launch_ms": dom_ms,
                 "peak_source": peak_src}

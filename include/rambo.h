@@ -169,7 +169,8 @@ size_t rambo_query_kmers_workspace(const rambo_t *h, uint64_t n);
 size_t rambo_query_seqs_workspace(const rambo_t *h, uint64_t n);
 /* Workspace with which a batch of n sequences over packed_bytes bytes can
  * take the tuned query path: query_path 2 (region-binned probing) needs room
- * for its probe records and runs only when the workspace passed to the call
+ * for its probe records, query_path 3 (content-ordered segments) for its
+ * segment lists, and each runs only when the workspace passed to the call
  * is at least this large; with less (down to rambo_query_seqs_workspace) the
  * call takes path 1.  Same answers either way. */
 size_t rambo_query_seqs_workspace_for(const rambo_t *h, uint64_t n, uint64_t packed_bytes);
@@ -342,6 +343,13 @@ typedef struct {
                                        /* region-binned probing (groups up to 64 B    */
                                        /* and a workspace from                         */
                                        /* rambo_query_seqs_workspace_for; otherwise    */
+                                       /* path 1); 3 = content-ordered segments: the   */
+                                       /* batch's k-mers cut at content-defined points */
+                                       /* and probed in the order of the segments'     */
+                                       /* keys, so k-mers repeated across queries find */
+                                       /* their groups in L2 (groups up to 64 B, eta   */
+                                       /* <= 4, CSR batches, a workspace from          */
+                                       /* rambo_query_seqs_workspace_for; otherwise    */
                                        /* path 1)                                      */
     uint32_t fused_tile_kmers;         /* path 1: k-mers per tile of a long query      */
     uint32_t fused_short_max;          /* path 1: queries with at most this many       */
@@ -375,8 +383,8 @@ typedef struct {
                                        /* 32768); regions hold a power-of-two number   */
                                        /* of groups and are at most 4096              */
     uint32_t bin_rows;                 /* path 2: group gathers a lane keeps in flight */
-                                       /* in the probe pass: 4, 6, 8 for 1, 2, 4 (and  */
-                                       /* 8); 0 = 1                                    */
+                                       /* in the probe pass: 4, 8, 12 for 1, 2 (or 0), */
+                                       /* 4 and 8                                      */
     uint32_t host_direct;              /* host-buffer calls: 1 = kernels write answers */
                                        /* straight into output buffers that are        */
                                        /* page-locked and device-addressable (each     */
@@ -411,6 +419,10 @@ typedef struct {
                                        /* launch needs fewer registers (default 0)     */
     uint32_t kmer_async;               /* the same for the single k-mer probe (16-byte */
                                        /* groups, eta <= 2; default 0)                 */
+    uint32_t seg_cut_bits;             /* query_path 3: a k-mer whose order hash has   */
+                                       /* this many low zero bits starts a segment     */
+                                       /* (segments of about 2^bits k-mers, at least   */
+                                       /* 2^(bits-1)); 0 = 6 (the default), <= 10      */
 } rambo_tuning_t;
 #define RAMBO_MAX_HOST_SLOTS 4
 

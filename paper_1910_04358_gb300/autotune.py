@@ -1,8 +1,9 @@
 """Autotuner for the query launch shapes.
 
 Picks, for one index and one representative batch, the query path (separate
-prefix/probe/expand launches or the persistent fused launch with
-length-bucketed queues), the probe grid (CTAs per SM), the minimum k-mers a
+prefix/probe/expand launches, the persistent fused launch with
+length-bucketed queues, region-binned probing, or content-ordered segments),
+the segment length, the probe grid (CTAs per SM), the minimum k-mers a
 warp takes, the fused path's tile size and short-query threshold, and the
 expansion grid and byte-table policy.  It times the batch under each
 candidate with CUDA events on the launching stream and insists that every
@@ -25,7 +26,7 @@ import os
 CACHE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 
 KNOBS = (
-    ("query_path", (0, 1, 2)),
+    ("query_path", (0, 1, 2, 3)),
     ("branch_priority", (0, 1, 2)),
     # expansion variant before its grid: a variant's best grid differs; the
     # filter takes precedence over the nibble table, so it is decided first
@@ -42,6 +43,7 @@ KNOBS = (
     ("kmer_probe_ctas_per_sm", (0, 1, 2, 3, 4)),
     ("bin_region_kib", (16384, 32768, 65536, 131072)),
     ("bin_rows", (1, 2, 4)),
+    ("seg_cut_bits", (4, 5, 6, 7, 8)),
     ("fused_tile_kmers", (256, 512, 1024, 2048, 4096)),
     ("fused_short_max", (64, 256, 1024, 4096)),
     ("probe_min_kmers_per_warp", (0, 256, 1024, 4096)),
@@ -67,12 +69,15 @@ def _time(run, reps: int):
 
 def effective_path(tuning, info) -> int:
     """Sequence query path the library takes for this tuning and geometry (the
-    binding always passes a workspace large enough for path 2): the binned
-    path for groups of at most 64 bytes, the fused path for groups of at most
-    512 bytes, else the separate launches."""
+    binding always passes a workspace large enough for paths 2 and 3, and
+    batches as CSR offsets): the binned path for groups of at most 64 bytes,
+    the content-ordered path for groups of at most 64 bytes and eta <= 4, the
+    fused path for groups of at most 512 bytes, else the separate launches."""
     g = info["group_bytes"]
     if tuning["query_path"] == 2 and g <= 64:
         return 2
+    if tuning["query_path"] == 3 and g <= 64 and info.get("eta", 1) <= 4:
+        return 3
     if tuning["query_path"] >= 1 and g <= 512:
         return 1
     return 0
@@ -102,6 +107,8 @@ def _one_pass(idx, run, outputs, ref, best_cfg, best_ms, knobs, reps, path, tria
         if knob in ("fused_tile_kmers", "fused_short_max", "fused_async") and path != 1:
             continue
         if knob in ("bin_region_kib", "bin_rows") and path != 2:
+            continue
+        if knob == "seg_cut_bits" and path != 3:
             continue
         for v in values:
             if best_cfg.get(knob) == v:

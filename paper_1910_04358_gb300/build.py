@@ -22,8 +22,8 @@ LIB = os.path.join(OUT_DIR, "librambo_gpu.so")
 SOURCES = ["rambo_api.cu", "rambo_kernels_probe.cu", "rambo_kernels_expand.cu",
            "rambo_kernels_fused.cu", "rambo_kernels_build.cu",
            "rambo_kernels_words.cu", "rambo_kernels_binned.cu",
-           "rambo_kernels_insert_binned.cu", "rambo_gather_probe.cu",
-           "rambo_noalloc.cu"]
+           "rambo_kernels_insert_binned.cu", "rambo_kernels_segments.cu",
+           "rambo_gather_probe.cu", "rambo_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]

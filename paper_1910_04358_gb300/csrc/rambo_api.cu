@@ -248,7 +248,7 @@ size_t kmers_ws(const Geometry &g, uint64_t n) { return align_up(n * (uint64_t)g
 struct BinLayout {
     uint32_t nb, shift, G;
     uint64_t cap;
-    size_t count_off, tile_off, rec_off, bytes;
+    size_t ctr_off, count_off, tile_off, rec_off, bytes;
 };
 BinLayout bin_layout(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
     const Geometry &g = h->g;
@@ -259,17 +259,55 @@ BinLayout bin_layout(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
     const uint64_t subs = (uint64_t)L.nb * L.G;
     const uint64_t expect = (4 * packed_bytes * g.eta + subs - 1) / subs;
     L.cap = (expect + expect / 8 + 64 + 1) / 2 * 2;  // even: 16-byte aligned record pairs
-    L.count_off = 0;
-    L.tile_off = align_up((size_t)subs * 4);
+    L.ctr_off = 0;  // the probe pass's work-item counter
+    L.count_off = 256;
+    L.tile_off = L.count_off + align_up((size_t)subs * 4);
     L.rec_off = L.tile_off + align_up((size_t)binned_max_tiles(g, n, packed_bytes) * 4);
     L.bytes = L.rec_off + (size_t)subs * L.cap * 8;
     return L;
 }
 bool use_binned(const rambo_t *h) { return h->tune.query_path == 2 && binned_supported(h->g); }
+
+// Extra workspace of the content-ordered path (after the sequence layout):
+// counters and bucket counts (zeroed per call), the recorded segments, the
+// ordered segments with their k-mer prefix, and the chunk map, for a CSR
+// batch of n items over packed_bytes (at most 4 * packed_bytes k-mers).
+constexpr uint32_t SEG_BUCKET_BITS = 16;
+struct SegLayout {
+    uint64_t cap, max_chunks;
+    uint32_t cut_grid, cut_bits, min_len;
+    size_t hdr_off, hdr_bytes, rbeg_off, rlen_off, rq_off, rkey_off, sbeg_off, send_off, sq_off, scum_off,
+        sbsum_off, chunk_off, bytes;
+};
+SegLayout seg_layout(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
+    SegLayout S{};
+    S.cut_bits = h->tune.seg_cut_bits ? h->tune.seg_cut_bits : 6;
+    S.min_len = 1u << (S.cut_bits - 1);
+    S.cut_grid = seg_cut_grid(h->sm_count);
+    const uint64_t max_kmers = 4 * packed_bytes;
+    S.cap = seg_capacity(max_kmers, n, S.min_len, S.cut_grid);
+    S.max_chunks = seg_max_chunks(max_kmers);
+    S.hdr_off = 0;
+    S.hdr_bytes = ALIGN + ((size_t)1 << SEG_BUCKET_BITS) * 4;
+    S.rbeg_off = align_up(S.hdr_bytes);
+    S.rlen_off = S.rbeg_off + align_up(S.cap * 8);
+    S.rq_off = S.rlen_off + align_up(S.cap * 4);
+    S.rkey_off = S.rq_off + align_up(S.cap * 4);
+    S.sbeg_off = S.rkey_off + align_up(S.cap * 4);
+    S.send_off = S.sbeg_off + align_up(S.cap * 8);
+    S.sq_off = S.send_off + align_up(S.cap * 8);
+    S.scum_off = S.sq_off + align_up(S.cap * 4);
+    S.sbsum_off = S.scum_off + align_up((S.cap + 1) * 8);
+    S.chunk_off = S.sbsum_off + align_up((kmer_prefix_block_sums(S.cap) + 1) * 8);
+    S.bytes = S.chunk_off + align_up(S.max_chunks * 4);
+    return S;
+}
+bool use_segments(const rambo_t *h) { return h->tune.query_path == 3 && segments_supported(h->g); }
 // Sequence workspace that lets the tuned path run on a batch over packed_bytes.
 size_t seq_ws_for(const rambo_t *h, uint64_t n, uint64_t packed_bytes) {
     size_t t = seq_ws(h->g, n).total;
     if (use_binned(h)) t += bin_layout(h, n, packed_bytes).bytes;
+    if (use_segments(h)) t += seg_layout(h, n, packed_bytes).bytes;
     return t;
 }
 
@@ -377,9 +415,73 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
             ba.G = B.G;
             ba.depth = binned_depth(h->tune.bin_rows);
             ba.cps = (uint32_t)((B.cap + BINNED_ITEM_RECS - 1) / BINNED_ITEM_RECS);
+            ba.item_ctr = reinterpret_cast<unsigned long long *>(bw + B.ctr_off);
             {
                 StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s, binned_launches());
                 RAMBO_TRY(launch_binned(ba, g, h->sm_count, s));
+            }
+            ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
+                         h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
+                         h->tune.expand_filter};
+            StageScope sc(h, RAMBO_STAGE_EXPAND, s, 1);
+            RAMBO_TRY(launch_expand(e, h->sm_count * (int)h->tune.expand_ctas_per_sm, h->sm_count, s));
+            return RAMBO_OK;
+        }
+    }
+    if (use_segments(h) && ends == offsets + 1) {
+        // content-ordered segments (CSR batches: at most 4 * packed_bytes k-mers)
+        const SegLayout S = seg_layout(h, n, packed_bytes);
+        if (ws_bytes >= L.total + S.bytes) {
+            {
+                StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
+                RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
+            }
+            char *sw = w + L.total;
+            RAMBO_TRY(cudaMemsetAsync(acc, 0xFF, n * (uint64_t)g.Gw * 4, s));
+            RAMBO_TRY(cudaMemsetAsync(sw + S.hdr_off, 0, S.hdr_bytes, s));
+            SegArgs sa{};
+            ProbeArgs &a = sa.p;
+            a.index = h->d_index;
+            a.m = g.m;
+            a.m_pow2 = (g.m & (g.m - 1)) == 0;
+            a.Gw = g.Gw;
+            a.eta = g.eta;
+            a.k = g.k;
+            a.seed32 = (uint32_t)g.seed;
+            a.packed = al.p;
+            a.packed_bytes = al.bytes;
+            a.base_shift = al.base_shift;
+            a.offsets = offsets;
+            a.ends = ends;
+            a.kcum = kcum;
+            a.n = n;
+            a.acc = acc;
+            a.err = h->d_err;
+            sa.cut_bits = S.cut_bits;
+            sa.min_len = S.min_len;
+            sa.bucket_shift = 32 - SEG_BUCKET_BITS;
+            sa.nbuckets = 1u << SEG_BUCKET_BITS;
+            sa.cap = S.cap;
+            sa.ctr = reinterpret_cast<unsigned long long *>(sw + S.hdr_off);
+            sa.bucket = reinterpret_cast<uint32_t *>(sw + S.hdr_off + ALIGN);
+            sa.raw_begin = reinterpret_cast<uint64_t *>(sw + S.rbeg_off);
+            sa.raw_len = reinterpret_cast<uint32_t *>(sw + S.rlen_off);
+            sa.raw_q = reinterpret_cast<uint32_t *>(sw + S.rq_off);
+            sa.raw_key = reinterpret_cast<uint32_t *>(sw + S.rkey_off);
+            sa.sbeg = reinterpret_cast<uint64_t *>(sw + S.sbeg_off);
+            sa.send = reinterpret_cast<uint64_t *>(sw + S.send_off);
+            sa.sq = reinterpret_cast<uint32_t *>(sw + S.sq_off);
+            sa.scum = reinterpret_cast<uint64_t *>(sw + S.scum_off);
+            sa.chunk_seg = reinterpret_cast<uint32_t *>(sw + S.chunk_off);
+            sa.max_chunks = S.max_chunks;
+            {
+                StageScope sc(h, RAMBO_STAGE_PROBE_SEQS, s,
+                              seg_launches_before_prefix() + kmer_prefix_launches(S.cap) +
+                                  seg_launches_after_prefix());
+                RAMBO_TRY(launch_seg_order(sa, S.cut_grid, h->sm_count, s));
+                RAMBO_TRY(launch_kmer_prefix(sa.sbeg, sa.send, S.cap, g.k, packed_bytes, sa.scum,
+                                             reinterpret_cast<uint64_t *>(sw + S.sbsum_off), h->d_err, s));
+                RAMBO_TRY(launch_seg_probe(sa, g, h->sm_count, s));
             }
             ExpandArgs e{acc, n, g.Gw, g.B, g.R, g.W, h->d_docbits, out, h->d_tab, h->tune.smem_docbits,
                          h->tune.use_nibble_table ? h->d_ntab : nullptr, h->d_phi, g.K,
@@ -873,6 +975,7 @@ int rambo_create(uint32_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     h->tune.host_slots = 3;
     h->tune.bin_region_kib = 32768;
     h->tune.bin_rows = 2;
+    h->tune.seg_cut_bits = 6;
     h->tune.host_direct = 0;
     h->tune.host_fused_ctas_per_sm = 1;
     h->tune.insert_mode = 2;
@@ -1368,13 +1471,14 @@ static int reserve_bins(rambo_t *h, const rambo_tuning_t *t) {
 int rambo_set_tuning(rambo_t *h, const rambo_tuning_t *t) {
     if (!h || !t) return RAMBO_EINVAL;
     if (t->probe_ctas_per_sm > 32 || t->expand_ctas_per_sm == 0 || t->expand_ctas_per_sm > 64 ||
-        t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 2 || t->fused_tile_kmers == 0 ||
+        t->probe_min_kmers_per_warp > (1u << 24) || t->query_path > 3 || t->fused_tile_kmers == 0 ||
         t->fused_tile_kmers > (1u << 24) || t->fused_short_max > (1u << 24) || t->smem_docbits > 1 ||
         t->use_nibble_table > 1 || t->expand_filter > 1 || t->early_exit > 1 ||
         t->early_exit_segment == 0 || (t->early_exit_segment & 127) || t->early_exit_segment > (1u << 24) ||
         t->kmer_probe_ctas_per_sm > 32 || t->host_chunk_kmers > (1u << 30) || t->branch_priority > 2 ||
         t->host_slots == 0 || t->host_slots > RAMBO_MAX_HOST_SLOTS || t->bin_region_kib > (1u << 22) ||
         (t->bin_rows != 0 && t->bin_rows != 1 && t->bin_rows != 2 && t->bin_rows != 4 && t->bin_rows != 8) ||
+        t->seg_cut_bits > 10 ||
         t->host_direct > 1 || t->host_fused_ctas_per_sm > 32 ||
         t->insert_mode > 3 || (t->insert_bin_records != 0 && t->insert_bin_records < 4096) ||
         t->fused_async > 1 || t->kmer_async > 1)

@@ -315,8 +315,9 @@ struct BinnedArgs {
     uint32_t nb, shift;
     uint32_t G;                     // scatter grid (binned_scatter_grid)
     uint32_t tile;                  // k-mers per scatter tile (binned_tile_kmers)
-    uint32_t depth;                 // probe pass: group gathers a lane keeps in flight (2, 4, 8)
+    uint32_t depth;                 // probe pass: 2, 4 or 8 for 4, 8 or 12 gathers a lane keeps in flight
     uint32_t cps;                   // work items per sub-bin: ceil(cap / BINNED_ITEM_RECS)
+    unsigned long long *item_ctr;   // probe pass: next work item, zeroed by k_bin_tiles
 };
 bool binned_supported(const Geometry &g);
 uint32_t binned_tile_kmers(const Geometry &g);
@@ -328,6 +329,40 @@ uint32_t binned_scatter_grid(const Geometry &g, uint32_t nb, int sm_count);
 uint32_t binned_bins(const Geometry &g, uint64_t region_bytes, uint32_t *shift);
 int binned_launches();
 cudaError_t launch_binned(const BinnedArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
+
+// Content-ordered segments (query path 3; groups of up to 64 bytes, eta <=
+// 4): the batch's k-mers cut at content-defined points into segments, the
+// segments ordered by the bucket of their key, then probed in that order.
+struct SegArgs {
+    ProbeArgs p;                  // index, hashing, the query batch (kcum over the
+                                  // queries), acc preset to all ones
+    uint32_t cut_bits;            // a k-mer starts a segment when the low cut_bits
+    uint32_t min_len;             //   bits of its order hash are zero and the last
+                                  //   start is min_len k-mers back (or it is forced)
+    uint32_t bucket_shift;        // bucket = key >> bucket_shift
+    uint32_t nbuckets;
+    uint64_t cap;                 // segment slots of every array below
+    unsigned long long *ctr;      // [0] segments recorded, [1] probe items claimed (zeroed)
+    uint32_t *bucket;             // nbuckets counts (zeroed) -> offsets -> cursors
+    uint64_t *raw_begin;          // recorded segments: first base (caller's base index)
+    uint32_t *raw_len, *raw_q, *raw_key;  //   k-mers, query, key
+    uint64_t *sbeg, *send;        // ordered segments as base ranges [sbeg, send)
+    uint32_t *sq;                 //   and their queries
+    uint64_t *scum;               // cap + 1: k-mer prefix of the ordered segments
+    uint32_t *chunk_seg;          // max_chunks: segment of every PSK-th ordered k-mer
+    uint64_t max_chunks;
+};
+bool segments_supported(const Geometry &g);
+uint32_t seg_cut_grid(int sm_count);
+// Segment slots a batch of n items with at most max_kmers k-mers can need.
+uint64_t seg_capacity(uint64_t max_kmers, uint64_t n, uint32_t min_len, uint32_t cut_grid);
+uint64_t seg_max_chunks(uint64_t max_kmers);
+int seg_launches_before_prefix();
+int seg_launches_after_prefix();
+// cut + bucket offsets + placement (after the query prefix; ctr and bucket zeroed)
+cudaError_t launch_seg_order(const SegArgs &a, uint32_t cut_grid, int sm_count, cudaStream_t s);
+// chunk map + probe (after the prefix of the ordered segments into scum)
+cudaError_t launch_seg_probe(const SegArgs &a, const Geometry &g, int sm_count, cudaStream_t s);
 
 // p.acc is unused (the bucket masks of long queries, and of queries with too
 // many passing buckets to expand in place, are e.acc).  Two launches after

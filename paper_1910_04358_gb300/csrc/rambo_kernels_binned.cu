@@ -16,13 +16,14 @@
 //            cursor in shared memory: no global atomics, and the records a
 //            tile adds to a sub-bin are one run of one query.  A record that
 //            finds its sub-bin full is probed on the spot.
-//   probe    work items are fixed chunks of sub-bins in region-major order,
-//            so at any moment the grid probes inside about one region that
-//            fits in L2, and each line comes from DRAM about once per batch.
-//            A lane walks consecutive records, ANDing the groups of a run in
-//            registers (the gathers staged in shared memory by cp.async, a
-//            few records ahead); a closed run is folded into its query's mask
-//            by one coalesced atomicAnd per 64 bytes.
+//   probe    work items are fixed chunks of sub-bins, claimed in
+//            region-major order from a counter, so at any moment the grid
+//            probes inside about one region that fits in L2, and each line
+//            comes from DRAM about once per batch.  The lanes that read one
+//            group walk a run of consecutive records, ANDing the groups of a
+//            query's run in registers with the next gathers in flight; a
+//            closed run is folded into its query's mask by one coalesced
+//            atomicAnd per mask row.
 // The per-query result does not depend on the order of the probes (a BFU
 // passes a query iff every probe of every k-mer finds its bit, so the bucket
 // mask is the AND of all probed groups), and neither does the sub-bin layout.
@@ -51,8 +52,10 @@ __device__ __forceinline__ void probe_direct(const ProbeArgs &p, uint32_t pos, u
 // tile_q[t] = the query whose k-mers tile t covers (one thread per query),
 // for the first max_tiles tiles (ranges may overlap, so a batch can have
 // more tiles than its packed bytes suggest; those are looked up by search).
+// Also zeroes the probe pass's work-item counter (the pass launches after).
 __global__ void k_bin_tiles(BinnedArgs a) {
     const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0 && a.item_ctr) *a.item_ctr = 0ull;
     if (q >= a.p.n) return;
     const uint64_t t1 = a.p.kcum[q + 1] < a.max_tiles ? a.p.kcum[q + 1] : a.max_tiles;
     for (uint64_t t = a.p.kcum[q]; t < t1; ++t) a.tile_q[t] = (uint32_t)q;
@@ -217,212 +220,174 @@ __device__ __forceinline__ void flush_run(uint32_t *acc, uint32_t q, uint32_t Gw
     }
 }
 
-// Shared-memory stride (words) of one staged group: groups of 16 bytes and
-// more are padded by 16 bytes, so that the 16-byte accesses of 8 consecutive
-// lanes fall in distinct banks.
-template <int GW>
-__host__ __device__ constexpr int slot_words() { return GW >= 4 ? GW + 4 : GW; }
-
-// Copies the GW-word group at `src` into shared memory `dst` (cp.async).
-template <int GW>
-__device__ __forceinline__ void stage_group(uint32_t *dst, const uint32_t *src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    if constexpr (GW >= 4) {
-#pragma unroll
-        for (int w = 0; w < GW; w += 4)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 4 * w), "l"(src + w) : "memory");
-    } else {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(GW * 4) : "memory");
-    }
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// Probe pass.  A group of GW words is
+// read by SL lanes, one 16-byte slice each (one lane holding the whole group
+// under 16 bytes), so a warp runs NS = 32 / SL streams side by side.  A work
+// item (BINNED_ITEM_RECS consecutive records of one sub-bin) is cut into NS
+// runs of PS consecutive records, one per stream; a stream walks its records
+// in order with the gathers of the next D records in flight in registers,
+// keeps the AND of the current run (records of one query) in registers, and
+// folds a closed run into its query's mask with one coalesced atomicAnd per
+// mask row.  One warp load instruction therefore reads NS whole groups (NS
+// lines), not 32 scattered slices.  The item's records are copied into the
+// warp's shared memory by coalesced cp.async (evict-first in L2: they are
+// read once), one item ahead; items are claimed from a counter in
+// region-major order, so the warps in flight stay within about one region
+// and the lines a region's probes share come from L2.
+constexpr int STREAM_WARPS = 8;
 
 template <int GW>
-__device__ __forceinline__ void and_staged(uint32_t (&run)[GW], const uint32_t *g) {
-    if constexpr (GW >= 4) {
-#pragma unroll
-        for (int w = 0; w < GW; w += 4) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(g + w);
-            run[w] &= v.x;
-            run[w + 1] &= v.y;
-            run[w + 2] &= v.z;
-            run[w + 3] &= v.w;
-        }
-    } else {
-#pragma unroll
-        for (int w = 0; w < GW; ++w) run[w] &= g[w];
-    }
+struct StreamShape {
+    static constexpr int SL = GW >= 4 ? GW / 4 : 1;     // lanes per group
+    static constexpr int SW = GW >= 4 ? 4 : GW;         // words per lane
+    static constexpr int NS = 32 / SL;                  // streams per warp
+    static constexpr int PS = (int)BINNED_ITEM_RECS / NS;  // records per stream and item
+    static constexpr int STRIDE = PS * 8 + 16;          // bytes per stream row (bank offset)
+    static constexpr int BUF = NS * STRIDE;             // bytes per item buffer
+};
+
+template <int GW>
+__host__ __device__ constexpr size_t stream_smem() {
+    return (size_t)STREAM_WARPS * 2 * StreamShape<GW>::BUF;
 }
 
+// Copies the valid records of item (sb, chunk0) into buf (stream-major rows),
+// 16 bytes (two records) per copy; commits one cp.async group either way.
 template <int GW>
-__device__ __forceinline__ void put_run(uint32_t *dst, const uint32_t (&run)[GW]) {
-    if constexpr (GW >= 4) {
+__device__ __forceinline__ void stage_item(unsigned char *buf, const unsigned long long *rec,
+                                           uint32_t valid, int lane, uint64_t policy) {
+    using S = StreamShape<GW>;
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(buf);
 #pragma unroll
-        for (int w = 0; w < GW; w += 4)
-            *reinterpret_cast<uint4 *>(dst + w) = make_uint4(run[w], run[w + 1], run[w + 2], run[w + 3]);
-    } else {
-#pragma unroll
-        for (int w = 0; w < GW; ++w) dst[w] = run[w];
-    }
-}
-
-// Folds queued runs [0, n) (rq[i] their queries) into their queries' masks:
-// LPR lanes per run, one 64-bit word each (32-bit for 4-byte groups), so a
-// run of a 64-byte group is one coalesced instruction.
-template <int GW>
-__device__ __forceinline__ void drain_runs(uint32_t *acc, const uint32_t *runs, const uint32_t *rq,
-                                           uint32_t n, int lane) {
-    constexpr int LPR = GW >= 16 ? 8 : (GW >= 2 ? GW / 2 : 1);
-    constexpr int RPI = 32 / LPR;
-    for (uint32_t i0 = 0; i0 < n; i0 += RPI) {
-        const uint32_t i = i0 + lane / LPR;
-        if (i < n) {
-            const uint32_t q = rq[i];
-            const uint32_t *r = runs + (size_t)i * slot_words<GW>();
-            if constexpr (GW == 1) {
-                if (r[0] != FULL) atomicAnd(acc + q, r[0]);
-            } else {
-                const uint32_t w = (lane % LPR) * 2;
-                const unsigned long long v = ((unsigned long long)r[w + 1] << 32) | r[w];
-                if (v != ~0ull) atomicAnd(reinterpret_cast<unsigned long long *>(acc + (uint64_t)q * GW + w), v);
-            }
+    for (int j = 0; j < (int)BINNED_ITEM_RECS / 64; ++j) {
+        const uint32_t t = (uint32_t)(j * 32 + lane);  // record pair
+        if (2 * t < valid) {
+            const uint32_t g = t / (S::PS / 2), i = 2 * (t % (S::PS / 2));
+            asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                             d0 + g * S::STRIDE + i * 8),
+                         "l"(rec + 2 * t), "l"(policy)
+                         : "memory");
         }
     }
-}
-
-// Probe pass.  Work item c = chunk (c % cps) of sub-bin (c / cps):
-// BINNED_ITEM_RECS consecutive records, 32 per lane.  A lane walks its
-// records in order: the group of each record is copied into the lane's
-// shared-memory ring (cp.async, no registers held) D records ahead of its
-// use, and the AND of the current run (records of one query) is kept in
-// registers.  A run ends where the query changes or the lane's records end;
-// it is queued in the warp's shared memory, and once 16 or more are queued
-// the warp folds them into the queries' masks together, one coalesced
-// atomicAnd instruction per mask row.
-constexpr int PROBE_WARPS = 4;
-constexpr int PROBE_PER = 16;     // records per lane and item
-constexpr int PROBE_QUEUE = 48;   // run queue: drained at 16, at most 32 added a step
-
-template <int GW, int D>
-__host__ __device__ constexpr size_t probe_smem() {
-    return (size_t)PROBE_WARPS * ((size_t)D * 32 * slot_words<GW>() * 4 +           // group ring
-                                  (size_t)PROBE_QUEUE * slot_words<GW>() * 4 +       // queued runs
-                                  (size_t)PROBE_QUEUE * 4);                          // their queries
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <int GW, int D>
-__global__ void __launch_bounds__(PROBE_WARPS * 32) k_bin_probe(BinnedArgs a) {
-    constexpr int SG = slot_words<GW>();
-    static_assert(BINNED_ITEM_RECS == 32 * PROBE_PER, "work item = 32 lanes x PROBE_PER records");
-    extern __shared__ __align__(16) uint32_t probe_smem_u32[];
+__global__ void __launch_bounds__(STREAM_WARPS * 32) k_bin_probe(BinnedArgs a) {
+    using S = StreamShape<GW>;
+    constexpr int SW = S::SW;
+    extern __shared__ __align__(16) unsigned char stream_smem_u8[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint32_t *ring = probe_smem_u32 + (size_t)wib * (D * 32 * SG + PROBE_QUEUE * SG + PROBE_QUEUE);
-    uint32_t *runs = ring + D * 32 * SG;
-    uint32_t *rq = runs + PROBE_QUEUE * SG;
-    uint32_t *slot0 = ring + (size_t)lane * SG;  // this lane's slot d is slot0 + d * 32 * SG
-    const uint64_t warp = (uint64_t)blockIdx.x * PROBE_WARPS + wib;
-    const uint64_t nwarps = (uint64_t)gridDim.x * PROBE_WARPS;
+    const int grp = lane / S::SL;
+    const uint32_t word0 = (uint32_t)(lane % S::SL) * SW;
+    unsigned char *bufs = stream_smem_u8 + (size_t)wib * 2 * S::BUF;
     const uint64_t items = (uint64_t)a.nb * a.G * a.cps;
     uint32_t *acc = a.p.acc;
     const uint32_t *index = a.p.index;
-    uint32_t queued = 0;  // warp-uniform
-    for (uint64_t c = warp; c < items; c += nwarps) {
-        const uint64_t sb = c / a.cps;
+    const unsigned long long *records = reinterpret_cast<const unsigned long long *>(a.records);
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+    // item c: sub-bin c / cps, records [chunk0, chunk0 + 512) of it, `valid` of them present
+    auto item_at = [&](uint64_t c, uint64_t &sb, uint32_t &chunk0, uint32_t &valid) {
+        sb = c / a.cps;
+        chunk0 = (uint32_t)(c - sb * a.cps) * BINNED_ITEM_RECS;
         const uint32_t cnt = a.sub_count[sb];
-        const uint32_t chunk0 = (uint32_t)(c - sb * a.cps) * BINNED_ITEM_RECS;
-        if (chunk0 >= cnt) continue;  // warp-uniform: an empty chunk
-        const uint32_t first = chunk0 + (uint32_t)lane * PROBE_PER;
-        const uint32_t mine = first < cnt ? (cnt - first < (uint32_t)PROBE_PER ? cnt - first : (uint32_t)PROBE_PER) : 0u;
-        const unsigned long long *rec =
-            reinterpret_cast<const unsigned long long *>(a.records) + sb * a.cap + first;
-        unsigned long long rr[D];  // the records whose groups are in flight
+        valid = chunk0 < cnt ? (cnt - chunk0 < BINNED_ITEM_RECS ? cnt - chunk0 : BINNED_ITEM_RECS) : 0u;
+    };
+    uint64_t cur = 0;
+    if (lane == 0) cur = atomicAdd(a.item_ctr, 1ull);
+    cur = __shfl_sync(FULL, cur, 0);
+    uint64_t sb;
+    uint32_t chunk0, valid;
+    if (cur < items) {
+        item_at(cur, sb, chunk0, valid);
+        stage_item<GW>(bufs, records + sb * a.cap + chunk0, valid, lane, policy);
+    }
+    int p = 0;
+    while (cur < items) {
+        uint64_t nxt = 0;
+        if (lane == 0) nxt = atomicAdd(a.item_ctr, 1ull);
+        nxt = __shfl_sync(FULL, nxt, 0);
+        uint64_t nsb = 0;
+        uint32_t nchunk0 = 0, nvalid = 0;
+        if (nxt < items) {
+            item_at(nxt, nsb, nchunk0, nvalid);
+            stage_item<GW>(bufs + (p ^ 1) * S::BUF, records + nsb * a.cap + nchunk0, nvalid, lane, policy);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncwarp();
+        // this stream's records of the item: ng of them, in row grp of the buffer
+        const int first = grp * S::PS;
+        const int ng = (int)valid > first ? ((int)valid - first < S::PS ? (int)valid - first : S::PS) : 0;
+        const unsigned long long *row =
+            reinterpret_cast<const unsigned long long *>(bufs + p * S::BUF + grp * S::STRIDE);
+        Slice<SW> buf[D];
+        uint32_t qq[D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            rr[i] = (uint32_t)i < mine ? __ldg(rec + i) : ~0ull;
-            if (rr[i] != ~0ull) stage_group<GW>(slot0 + i * 32 * SG, index + (rr[i] >> 32) * GW);
-            cp_commit();
+        for (int d = 0; d < D; ++d) {
+            if (d < ng) {
+                const unsigned long long x = row[d];
+                qq[d] = (uint32_t)x;
+                buf[d] = ld_slice<SW>(index + (x >> 32) * GW + word0);
+            }
         }
         uint32_t cq = NONE;
-        uint32_t run[GW];
-#pragma unroll
-        for (int w = 0; w < GW; ++w) run[w] = FULL;
+        Slice<SW> run;
+        slice_ones(run);
 #pragma unroll 1
-        for (int i0 = 0; i0 < PROBE_PER; i0 += D) {
+        for (int i0 = 0; i0 < ng; i0 += D) {
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const int i = i0 + d;
-                cp_wait<D - 1>();  // record i's group has landed in slot d
-                const unsigned long long x = rr[d];
-                const uint32_t q = x != ~0ull ? (uint32_t)x : NONE;
-                const bool closes = cq != NONE && q != cq;
-                const uint32_t ballot = __ballot_sync(FULL, closes);
-                if (closes) {
-                    const uint32_t at = queued + __popc(ballot & ((1u << lane) - 1u));
-                    rq[at] = cq;
-                    put_run<GW>(runs + at * SG, run);
-                }
-                queued += __popc(ballot);
-                if (q != cq) {
-                    cq = q;
-#pragma unroll
-                    for (int w = 0; w < GW; ++w) run[w] = FULL;
-                }
-                if (x != ~0ull) and_staged<GW>(run, slot0 + d * 32 * SG);
-                // the slot is free again: the record D ahead
-                const uint32_t nx = (uint32_t)(i + D);
-                rr[d] = nx < mine ? __ldg(rec + nx) : ~0ull;
-                if (rr[d] != ~0ull) stage_group<GW>(slot0 + d * 32 * SG, index + (rr[d] >> 32) * GW);
-                cp_commit();
-                if (queued >= 16) {
-                    __syncwarp();
-                    drain_runs<GW>(acc, runs, rq, queued, lane);
-                    __syncwarp();
-                    queued = 0;
+                if (i < ng) {
+                    const uint32_t q = qq[d];
+                    if (q != cq) {
+                        if (cq != NONE) flush_run<SW>(acc, cq, GW, word0, run);
+                        cq = q;
+                        slice_ones(run);
+                    }
+                    slice_and(run, buf[d]);
+                    if (i + D < ng) {
+                        const unsigned long long y = row[i + D];
+                        qq[d] = (uint32_t)y;
+                        buf[d] = ld_slice<SW>(index + (y >> 32) * GW + word0);
+                    }
                 }
             }
         }
-        // the lanes' last runs
-        const bool last = cq != NONE;
-        const uint32_t ballot = __ballot_sync(FULL, last);
-        if (last) {
-            const uint32_t at = queued + __popc(ballot & ((1u << lane) - 1u));
-            rq[at] = cq;
-            put_run<GW>(runs + at * SG, run);
-        }
-        queued += __popc(ballot);
-        if (queued >= 16) {
-            __syncwarp();
-            drain_runs<GW>(acc, runs, rq, queued, lane);
-            __syncwarp();
-            queued = 0;
-        }
+        if (cq != NONE) flush_run<SW>(acc, cq, GW, word0, run);
+        __syncwarp();  // every lane is done with this buffer before it is refilled
+        cur = nxt;
+        sb = nsb;
+        chunk0 = nchunk0;
+        valid = nvalid;
+        p ^= 1;
     }
-    __syncwarp();
-    drain_runs<GW>(acc, runs, rq, queued, lane);
-    cp_wait<0>();
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 template <int GW, int D>
-cudaError_t launch_probe_d(const BinnedArgs &a, int sm_count, cudaStream_t s) {
-    constexpr size_t smem = probe_smem<GW, D>();
-    cudaError_t e = cudaFuncSetAttribute(k_bin_probe<GW, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_streams_d(const BinnedArgs &a, int sm_count, cudaStream_t s) {
+    constexpr size_t smem = stream_smem<GW>();
+    cudaError_t e = cudaFuncSetAttribute(k_bin_probe<GW, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bin_probe<GW, D>, PROBE_WARPS * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bin_probe<GW, D>, STREAM_WARPS * 32, smem);
     if (e != cudaSuccess) return e;
-    k_bin_probe<GW, D><<<(occ > 0 ? occ : 1) * sm_count, PROBE_WARPS * 32, smem, s>>>(a);
+    k_bin_probe<GW, D><<<(occ > 0 ? occ : 1) * sm_count, STREAM_WARPS * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int GW>
 cudaError_t launch_probe_pass(const BinnedArgs &a, int sm_count, cudaStream_t s) {
     switch (a.depth) {
-        case 2: return launch_probe_d<GW, 2>(a, sm_count, s);
-        case 4: return launch_probe_d<GW, 4>(a, sm_count, s);
-        default: return launch_probe_d<GW, 8>(a, sm_count, s);
+        case 2: return launch_streams_d<GW, 4>(a, sm_count, s);
+        case 4: return launch_streams_d<GW, 8>(a, sm_count, s);
+        default: return launch_streams_d<GW, 12>(a, sm_count, s);
     }
 }
 
@@ -483,7 +448,7 @@ cudaError_t launch_binned(const BinnedArgs &a, const Geometry &g, int sm_count, 
     if (!binned_supported(g) || a.tile == 0 || (uint64_t)a.tile * a.p.eta > BINNED_TILE_RECS ||
         a.nb == 0 || a.nb > BIN_MAX || a.G == 0 || (a.cap & 1) ||
         (a.depth != 2 && a.depth != 4 && a.depth != 8) ||
-        a.cps != (uint32_t)((a.cap + BINNED_ITEM_RECS - 1) / BINNED_ITEM_RECS))
+        a.cps != (uint32_t)((a.cap + BINNED_ITEM_RECS - 1) / BINNED_ITEM_RECS) || a.item_ctr == nullptr)
         return cudaErrorInvalidValue;
     if (a.p.n == 0) return cudaSuccess;
     k_bin_tiles<<<(unsigned)((a.p.n + 255) / 256), 256, 0, s>>>(a);

@@ -173,7 +173,7 @@ TUNING_FIELDS = ("probe_ctas_per_sm", "probe_min_kmers_per_warp", "expand_ctas_p
                  "host_slots", "bin_region_kib", "bin_rows", "host_direct",
                  "host_fused_ctas_per_sm",
                  "insert_mode", "insert_bin_records", "fused_async",
-                 "kmer_async")
+                 "kmer_async", "seg_cut_bits")
 
 
 class _Tuning(C.Structure):

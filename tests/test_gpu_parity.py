@@ -147,7 +147,7 @@ SWEEP = [
 ]
 
 
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 3])
 @pytest.mark.parametrize("K,B,R,m,eta,k", SWEEP)
 def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k, path):
     p = synth.Params(K=K, B=B, R=R, m=m, eta=eta, k=k, seed=K + B)
@@ -158,7 +158,9 @@ def test_parameter_sweep(rambo_lib, K, B, R, m, eta, k, path):
     idx = gpu_index(rambo_lib, p, corpus, chunks=3)
     # path 1 (persistent fused launch) with small tiles so long queries span tiles
     # path 2 (region-binned) with 1 KiB regions so the batch spans many bins
-    idx.set_tuning(query_path=path, fused_tile_kmers=64, fused_short_max=40, bin_region_kib=1)
+    # path 3 (content-ordered segments) with segments of about 4 k-mers
+    idx.set_tuning(query_path=path, fused_tile_kmers=64, fused_short_max=40, bin_region_kib=1,
+                   seg_cut_bits=2)
     assert_index_equal(idx, o, p)
     assert_docbits_equal(idx, o, p)
     assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets),
@@ -355,9 +357,9 @@ def test_argument_errors(rambo_lib):
     assert np.array_equal(rambo_lib.as_u32(ok_s), idx.query_seqs(packed, np.array([0, 40], np.uint64)))
     # tuning knobs out of range are refused and leave the tuning unchanged
     before = idx.get_tuning()
-    for bad in (dict(query_path=3), dict(host_slots=0), dict(host_slots=5), dict(bin_rows=3),
+    for bad in (dict(query_path=4), dict(host_slots=0), dict(host_slots=5), dict(bin_rows=3),
                 dict(insert_mode=4), dict(insert_bin_records=100), dict(fused_async=2), dict(kmer_async=2),
-                dict(early_exit_segment=100)):
+                dict(seg_cut_bits=11), dict(early_exit_segment=100)):
         with pytest.raises(rambo_lib.RamboError):
             idx.set_tuning(**bad)
     assert idx.get_tuning() == before
@@ -482,7 +484,11 @@ def test_binned_path_matches_oracle(rambo_lib, K, B, R, m, eta, region_kib, max_
     want = o.query_seqs(q.packed, q.offsets)
     idx = gpu_index(rambo_lib, p, corpus)
     idx.set_tuning(query_path=2, bin_region_kib=region_kib)
-    assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want)
+    # the probe pass at every depth
+    for rows in (1, 2, 4):
+        idx.set_tuning(bin_rows=rows)
+        assert np.array_equal(gpu_query_seqs(rambo_lib, idx, q.packed, q.offsets), want), rows
+    idx.set_tuning(bin_rows=2)
     assert np.array_equal(idx.query_seqs(q.packed, q.offsets), want)
     # a workspace without room for the records: the call takes path 1
     d_p, d_o = _dev(q.packed, np.uint8), _dev(q.offsets.astype(np.uint64), np.int64)
@@ -515,6 +521,65 @@ def test_binned_path_overflow_probes_directly(rambo_lib, B, R, doc_len):
     out = idx.query_ranges_dev(_dev(corpus.packed, np.uint8), begins, ends)
     idx.sync()
     assert np.array_equal(rambo_lib.as_u32(out), np.repeat(one, n, axis=0))
+
+
+# ------------------------------------------ content-ordered segments (path 3)
+
+@pytest.mark.parametrize("K,B,R,m,eta", [
+    (300, 100, 5, 1 << 16, 2),          # 64-byte groups (four lanes per group)
+    (150, 40, 4, (1 << 16) + 77, 3),     # 32-byte groups, eta 3, odd m
+    (300, 32, 4, 1 << 18, 2),           # 16-byte groups (one lane)
+    (200, 20, 3, 1 << 16, 4),           # 8-byte groups, eta 4
+    (64, 8, 2, 1 << 14, 1),             # 4-byte groups, eta 1
+    (500, 64, 6, 12289, 5),             # eta 5: path 3 unsupported, path 1 runs
+])
+def test_segment_path_matches_oracle(rambo_lib, K, B, R, m, eta):
+    torch = _torch()
+    p = synth.Params(K=K, B=B, R=R, m=m, eta=eta, k=31, seed=5)
+    rng = np.random.default_rng(K + B + eta)
+    corpus = synth.family_corpus(rng, p, n_seeds=8, doc_len=14000, sub_rate=0.005)
+    # lengths from empty to several cut-pass warp ranges (2,048 k-mers each);
+    # most queries from documents, so segments repeat across queries
+    lengths = np.concatenate([rng.integers(0, 3000, size=250), [0, 5, 30, 31, 32, 13000, 9000]])
+    q = synth.sample_queries(rng, corpus, lengths, 0.8, err_rate=0.001)
+    # low-complexity queries: every k-mer (or every other) identical, so each
+    # position is a cut candidate and only the minimum length spaces them
+    extra = [np.zeros(700, np.uint8), np.tile(np.array([0, 1], np.uint8), 600),
+             np.tile(np.array([2, 3, 1], np.uint8), 500)]
+    qs = [synth.unpack_bases(q.packed, int(q.offsets[i]), int(q.offsets[i + 1] - q.offsets[i]))
+          for i in range(q.n)] + extra
+    qp, qo = synth.pack_many(qs)
+    o = oracle_index(p, corpus)
+    want = o.query_seqs(qp, qo)
+    idx = gpu_index(rambo_lib, p, corpus)
+    for bits in (1, 4, 8):
+        idx.set_tuning(query_path=3, seg_cut_bits=bits)
+        assert np.array_equal(gpu_query_seqs(rambo_lib, idx, qp, qo), want), bits
+    # twice in a row through one workspace (counters and buckets start over)
+    idx.set_tuning(seg_cut_bits=4)
+    d_p, d_o = _dev(qp, np.uint8), _dev(qo.astype(np.uint64), np.int64)
+    need = idx.workspace_bytes("seqs", qo.size - 1, qp.size)
+    buf = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    for _ in range(2):
+        out = idx.query_seqs_dev(d_p, d_o, workspace=(ptr, need))
+        idx.sync()
+        assert np.array_equal(rambo_lib.as_u32(out), want)
+    # misaligned packed pointer, and the host-buffer call
+    pad = _dev(np.concatenate([np.zeros(5, np.uint8), qp]), np.uint8)[5:]
+    out = idx.query_seqs_dev(pad, d_o)
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(out), want)
+    assert np.array_equal(idx.query_seqs(qp, qo), want)
+    # separate ranges (not a CSR batch) and a workspace without room for the
+    # segments: path 1 answers
+    out = idx.query_ranges_dev(d_p, d_o[:-1].contiguous(), d_o[1:].contiguous())
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(out), want)
+    small = idx.workspace_bytes("seqs", qo.size - 1)
+    out = idx.query_seqs_dev(d_p, d_o, workspace=(ptr, small))
+    idx.sync()
+    assert np.array_equal(rambo_lib.as_u32(out), want)
 
 
 # ------------------------------------------------ mixed batches (both kinds)

@@ -26,6 +26,9 @@ def test_bench_effective_path():
     assert bench.effective_path(t(1), {"group_bytes": 512}) == 1
     assert bench.effective_path(t(1), {"group_bytes": 1024}) == 0
     assert bench.effective_path(t(0), {"group_bytes": 16}) == 0
+    assert bench.effective_path(t(3), {"group_bytes": 64, "eta": 2}) == 3
+    assert bench.effective_path(t(3), {"group_bytes": 64, "eta": 5}) == 1
+    assert bench.effective_path(t(3), {"group_bytes": 128, "eta": 2}) == 1
 
 
 class _FakeIndex:
@@ -56,6 +59,8 @@ def _fused_cost(t, info):
         return 1.10
     if p == 2:
         return 1.20 - (0.01 if t["bin_rows"] == 4 else 0.0)
+    if p == 3:
+        return 1.15 - (0.01 if t["seg_cut_bits"] == 7 else 0.0)
     return 1.105 - 0.03 * (t["fused_tile_kmers"] == 256) - 0.03 * (t["fused_short_max"] == 256)
 
 
@@ -63,23 +68,26 @@ def test_autotune_descends_from_every_path_the_geometry_runs(monkeypatch):
     import torch
     from paper_1910_04358_gb300 import autotune
     out = torch.zeros(4, dtype=torch.int32)
-    # 256-byte groups: a request for the binned path runs the fused one, so
-    # only paths 0 and 1 are searched, and the fused knobs are tuned
+    # 256-byte groups: a request for the binned or the segment path runs the
+    # fused one, so only paths 0 and 1 are searched, and the fused knobs are tuned
     idx = _FakeIndex(256)
     monkeypatch.setattr(autotune, "_time", lambda run, reps: _fused_cost(idx.t, idx.info))
     res = autotune.autotune(idx, lambda: None, lambda: [out], reps=1)
     assert autotune.effective_path(res["best"], idx.info) == 1
     assert res["best"]["fused_tile_kmers"] == 256 and res["best"]["fused_short_max"] == 256
-    assert not any(tr["tuning"]["query_path"] == 2 for tr in res["trials"])
+    assert not any(tr["tuning"]["query_path"] in (2, 3) for tr in res["trials"])
     assert not any(tr["tuning"]["bin_rows"] != dict(autotune.KNOBS)["bin_rows"][0] for tr in res["trials"])
     assert idx.get_tuning() == res["best"]
-    # 16-byte groups: three distinct paths; the binned knobs vary only there
+    # 16-byte groups: four distinct paths; the binned and segment knobs vary
+    # only on their own paths
     idx = _FakeIndex(16)
     monkeypatch.setattr(autotune, "_time", lambda run, reps: _fused_cost(idx.t, idx.info))
     res = autotune.autotune(idx, lambda: None, lambda: [out], reps=1)
-    assert {tr["tuning"]["query_path"] for tr in res["trials"]} == {0, 1, 2}
+    assert {tr["tuning"]["query_path"] for tr in res["trials"]} == {0, 1, 2, 3}
     assert all(tr["tuning"]["query_path"] == 2 for tr in res["trials"]
                if tr["tuning"]["bin_rows"] == 4)
+    assert all(tr["tuning"]["query_path"] == 3 for tr in res["trials"]
+               if tr["tuning"]["seg_cut_bits"] == 7)
     assert res["best"]["query_path"] == 1
 
 

@@ -22,7 +22,7 @@ def _dev(torch, a, dt):
 
 
 @pytest.mark.parametrize("tuning", [dict(query_path=0), dict(query_path=1),
-                                    dict(query_path=2, bin_region_kib=256)])
+                                    dict(query_path=2, bin_region_kib=256), dict(query_path=3)])
 def test_noalloc_query_matches_workspace_query_and_oracle_twice(rambo_lib, tuning):
     # each query path the tuning can pick (path 2 with regions large enough
     # that its record bins fit the static scratch), two different batches in
@@ -42,7 +42,7 @@ def test_noalloc_query_matches_workspace_query_and_oracle_twice(rambo_lib, tunin
     for call, n in enumerate((300, 211)):
         q = synth.sample_queries(rng, corpus, rng.integers(20, 600, size=n), 0.6)
         packed, offs = _dev(torch, q.packed, np.uint8), _dev(torch, q.offsets, np.int64)
-        if tuning["query_path"] == 2:  # the binned layout fits the scratch for this batch
+        if tuning["query_path"] >= 2:  # the binned / segment layout fits the scratch for this batch
             assert idx.workspace_bytes("seqs", n, packed.numel()) <= STATIC_SCRATCH_BYTES
         want = idx.query_seqs_dev(packed, offs)
         idx.sync()
