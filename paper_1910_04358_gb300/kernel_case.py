@@ -39,6 +39,7 @@ def main(argv=None):
     ap.add_argument("--n-docs", type=int, default=None, help="fewer documents (same geometry)")
     ap.add_argument("--m", type=int, default=None, help="bits per filter (smaller index)")
     ap.add_argument("--n-queries", type=int, default=None, help="fewer sequence queries (large)")
+    ap.add_argument("--n-seeds", type=int, default=None, help="fewer seed genomes (large)")
     ap.add_argument("--epochs", type=int, default=3, help="insert epochs before the query (stream)")
     ap.add_argument("--buf-gb", type=float, nargs="+", default=[1.0, 64.0], help="gather: buffer sizes")
     ap.add_argument("--records", type=int, nargs="+", default=[16, 32, 64, 128, 256, 512],
@@ -59,6 +60,8 @@ def main(argv=None):
         kw = {"n_docs": a.n_docs}
         if a.n_queries:
             kw["n_queries"] = a.n_queries
+        if a.n_seeds:
+            kw["n_seeds"] = a.n_seeds
         corpus, q = synth.large_workload(**kw)
         kmers = np.zeros(0, np.uint64)
     p = corpus.params

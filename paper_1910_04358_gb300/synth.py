@@ -288,15 +288,17 @@ def medium_workload(n_docs: int | None = None, doc_len: int = 1_000_000, n_kmers
     return corpus, kmers, q
 
 
-def large_workload(n_docs: int | None = None, doc_len: int = 500_000, n_queries: int = 100_000):
+def large_workload(n_docs: int | None = None, doc_len: int = 500_000, n_queries: int = 100_000,
+                   n_seeds: int = 200):
     """10,000 x 500 kbp documents from 200 seeds, 0.5% substitutions and 0.05%
     indels; 10^5 queries of length U[31, 5000], 70% from documents with 0.1%
-    read errors."""
+    read errors.  A reduced copy that keeps the batch's repetition (k-mers
+    shared across queries) scales documents, seeds and queries together."""
     p = WORKLOAD_PARAMS[LARGE]
     if n_docs is not None:
         p = Params(K=n_docs, B=p.B, R=p.R, m=p.m, eta=p.eta)
     rng = rng_for(LARGE)
-    corpus = family_corpus(rng, p, 200, doc_len, 0.005, 0.0005)
+    corpus = family_corpus(rng, p, n_seeds, doc_len, 0.005, 0.0005)
     lengths = rng.integers(31, 5001, size=n_queries)
     q = sample_queries(rng, corpus, lengths, 0.7, err_rate=0.001)
     return corpus, q
