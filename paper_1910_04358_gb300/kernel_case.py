@@ -88,15 +88,22 @@ def main(argv=None):
     if a.case == "kmers":
         dk = dev(kmers, np.int64)
         out = torch.empty((kmers.size, idx.W), dtype=torch.int32, device="cuda")
-        for _ in range(a.reps):
-            idx.query_kmers_dev(dk, out=out)
+        run = lambda: idx.query_kmers_dev(dk, out=out)
     else:
         dp, do = dev(q.packed, np.uint8), dev(q.offsets, np.int64)
         out = torch.empty((q.n, idx.W), dtype=torch.int32, device="cuda")
-        for _ in range(a.reps):
-            idx.query_seqs_dev(dp, do, out=out)
+        run = lambda: idx.query_seqs_dev(dp, do, out=out)
+    ms = []
+    for _ in range(a.reps):  # each call timed with CUDA events on the launching stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
     idx.sync()
-    print("ok", a.case, a.workload, int(out.sum().item()))
+    print("ok", a.case, a.workload, int(out.sum().item()),
+          "ms per call: best %.3f (of %d; the first includes setup)" % (min(ms[1:] or ms), len(ms)))
     return 0
 
 
