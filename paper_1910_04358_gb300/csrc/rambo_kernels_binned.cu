@@ -33,7 +33,6 @@ namespace rgpu {
 namespace {
 
 constexpr int SCATTER_THREADS = 512;
-constexpr int BIN_THREADS = 256;
 constexpr uint64_t BIN_MAX = 4096;   // most bins (index regions) per batch
 
 __device__ __forceinline__ uint64_t make_rec(uint32_t pos, uint32_t q) {
