@@ -431,7 +431,8 @@ int query_seqs_enqueue(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t p
     if (use_segments(h) && ends == offsets + 1) {
         // content-ordered segments (CSR batches: at most 4 * packed_bytes k-mers)
         const SegLayout S = seg_layout(h, n, packed_bytes);
-        if (ws_bytes >= L.total + S.bytes) {
+        // (segment and query indexes are 32-bit: larger batches take path 1)
+        if (ws_bytes >= L.total + S.bytes && S.cap <= 0xffffffffull) {
             {
                 StageScope sc(h, RAMBO_STAGE_PREFIX, s, kmer_prefix_launches(n));
                 RAMBO_TRY(launch_kmer_prefix(offsets, ends, n, g.k, packed_bytes, kcum, bsum, h->d_err, s));
