@@ -247,8 +247,9 @@ int rambo_query_batch_dev(rambo_t *h, uint64_t n_kmers, const uint64_t *kmers, u
  * well) this entry point must not be called again in the same process.
  * Every call on a device shares the one array, so calls whose work can
  * overlap on the GPU (different streams, or handles on the same device)
- * race: serialise them.  With query_path 2 the region-binned path runs when
- * its record bins fit the array as well, else path 1. */
+ * race: serialise them.  With query_path 2 or 3 the region-binned or the
+ * content-ordered path runs when its records or segment lists fit the array
+ * as well, else path 1. */
 #define RAMBO_STATIC_SCRATCH_BYTES (8u << 20)
 int rambo_query_seqs_noalloc(rambo_t *h, uint64_t n, const uint8_t *packed, uint64_t packed_bytes,
                              const uint64_t *base_offsets, uint32_t *out, void *stream);
