@@ -40,6 +40,7 @@ namespace {
 constexpr int SEG_THREADS = 256;
 constexpr uint32_t SEG_MIN_RANGE = 2048;  // k-mers per warp in the cut pass, at least
 constexpr int SEG_PSK = 16;               // k-mers per lane group and work item
+constexpr uint64_t SEG_MAX_LEN = 1ull << 30;  // a start is forced this far after the last one
 
 // Order hash of a canonical code: the high word of one multiply-xorshift round
 // (only the order of the probes depends on it).
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_cut(SegArgs a) {
             const uint64_t qk = g - p.kcum[qlane];
             beg = p.offsets[qlane] + qk;
             key = order_hash(canonical_from_window(base_window(p.packed, p.packed_bytes, beg + p.base_shift), p.k));
-            forced = qk == 0 || g == c0;
+            forced = qk == 0 || g == c0 || g - last_kept >= SEG_MAX_LEN;  // (lengths fit 32 bits)
         }
         const uint32_t cm = __ballot_sync(FULL, valid && (forced || (key & cut_mask) == 0));
         const uint32_t fm = __ballot_sync(FULL, valid && forced);
@@ -376,9 +377,9 @@ uint32_t seg_cut_grid(int sm_count) {
 
 uint64_t seg_capacity(uint64_t max_kmers, uint64_t n, uint32_t min_len, uint32_t cut_grid) {
     // starts that are not forced are min_len apart; forced ones are query
-    // starts and warp-range starts
+    // starts, warp-range starts and one per SEG_MAX_LEN k-mers
     const uint64_t ml = min_len ? min_len : 1;
-    return (max_kmers + ml - 1) / ml + n + (uint64_t)cut_grid * (SEG_THREADS / 32) + 1;
+    return (max_kmers + ml - 1) / ml + n + (uint64_t)cut_grid * (SEG_THREADS / 32) + max_kmers / SEG_MAX_LEN + 1;
 }
 
 uint64_t seg_max_chunks(uint64_t max_kmers) { return (max_kmers + SEG_PSK - 1) / SEG_PSK + 1; }
