@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(SEG_THREADS) k_seg_cut(SegArgs a) {
     uint64_t qlane = find_query(p.kcum, p.n, c0);
     const uint32_t cut_mask = (1u << a.cut_bits) - 1u;
     // the open segment (warp-uniform): first k-mer index, first base, key, query
-    uint64_t o_start = ~0ull, o_beg = 0, last_kept = 0;
+    uint64_t o_start = ~0ull, o_beg = 0, last_kept = c0;  // (c0 is a forced start)
     uint32_t o_key = 0, o_q = 0;
     uint32_t buffered = 0;  // warp-uniform
     auto flush = [&]() {
@@ -377,9 +377,11 @@ uint32_t seg_cut_grid(int sm_count) {
 
 uint64_t seg_capacity(uint64_t max_kmers, uint64_t n, uint32_t min_len, uint32_t cut_grid) {
     // starts that are not forced are min_len apart; forced ones are query
-    // starts, warp-range starts and one per SEG_MAX_LEN k-mers
+    // starts, warp-range starts, and at most one step's 32 k-mers per
+    // SEG_MAX_LEN k-mers without a start
     const uint64_t ml = min_len ? min_len : 1;
-    return (max_kmers + ml - 1) / ml + n + (uint64_t)cut_grid * (SEG_THREADS / 32) + max_kmers / SEG_MAX_LEN + 1;
+    return (max_kmers + ml - 1) / ml + n + (uint64_t)cut_grid * (SEG_THREADS / 32) +
+           32 * (max_kmers / SEG_MAX_LEN) + 1;
 }
 
 uint64_t seg_max_chunks(uint64_t max_kmers) { return (max_kmers + SEG_PSK - 1) / SEG_PSK + 1; }
